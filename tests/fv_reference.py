@@ -1,0 +1,76 @@
+"""Independent uniform-grid finite-volume solver and exact-solution helpers for
+the oracle pins.  It is the textbook FV scheme of Sec. 2 (Eq. 2) with the
+explicit RK methods of Sec. 3 in Butcher form (Eqs. 8-9), written
+vectorised over a uniform periodic 1D grid with numpy -- a different
+formulation from the oracle's per-leaf compact-form loops."""
+from __future__ import annotations
+
+import numpy as np
+
+# Butcher tableaux from Sec. 3: c1=0, c2=a21=1, b=(1/2,1/2) for RK2;
+# c3=1/2, a31=a32=1/4, b=(1/6,1/6,2/3) for RK3
+BUTCHER = {
+    2: (np.array([[0, 0], [1, 0]], float), np.array([0.5, 0.5])),
+    3: (np.array([[0, 0, 0], [1, 0, 0], [0.25, 0.25, 0]], float),
+        np.array([1 / 6, 1 / 6, 2 / 3])),
+}
+
+
+def _minmod(a, b):
+    return np.where(a * b <= 0, 0.0, np.where(np.abs(a) < np.abs(b), a, b))
+
+
+def burgers_rhs(u, h):
+    """-(F_{i+1/2} - F_{i-1/2})/h, MUSCL-minmod + Godunov, periodic."""
+    um, up, upp = np.roll(u, 1), np.roll(u, -1), np.roll(u, -2)
+    uL = u + 0.5 * _minmod(u - um, up - u)
+    uR = up - 0.5 * _minmod(up - u, upp - up)
+    fL, fR = 0.5 * uL ** 2, 0.5 * uR ** 2
+    rare = np.where(uL > 0, fL, np.where(uR < 0, fR, 0.0))
+    F = np.where(uL <= uR, rare, np.maximum(fL, fR))  # flux at i+1/2
+    return -(F - np.roll(F, 1)) / h
+
+
+def advection_rhs(u, h, a=1.0):
+    F = a * (u + np.roll(u, -1)) / 2.0
+    return -(F - np.roll(F, 1)) / h
+
+
+def rk_solve(u0, rhs, dt, nsteps, order):
+    A, b = BUTCHER[order]
+    u = u0.copy()
+    s = len(b)
+    for _ in range(nsteps):
+        K = []
+        for i in range(s):
+            ui = u + sum(A[i, j] * K[j] for j in range(i))
+            K.append(dt * rhs(ui))
+        u = u + sum(b[i] * K[i] for i in range(s))
+    return u
+
+
+def burgers_exact_sine(x, t, iters=60):
+    """u = sin(2 pi (x - u t)) by Newton, valid before the shock (t < 1/(2 pi))."""
+    u = np.sin(2 * np.pi * x)
+    for _ in range(iters):
+        g = u - np.sin(2 * np.pi * (x - u * t))
+        dg = 1 + 2 * np.pi * t * np.cos(2 * np.pi * (x - u * t))
+        u = u - g / dg
+    return u
+
+
+GL8_X, GL8_W = np.polynomial.legendre.leggauss(8)
+
+
+def cell_average_1d(fun, n, lo=0.0, hi=1.0):
+    h = (hi - lo) / n
+    c = lo + (np.arange(n) + 0.5) * h
+    return sum(0.5 * w * fun(c + 0.5 * h * x) for x, w in zip(GL8_X, GL8_W))
+
+
+def poly_cell_average(coeffs, a, b):
+    """exact mean of sum_k coeffs[k] x^k over [a, b]"""
+    out = 0.0
+    for k, ck in enumerate(coeffs):
+        out = out + ck * (b ** (k + 1) - a ** (k + 1)) / ((k + 1) * (b - a))
+    return out
