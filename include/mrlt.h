@@ -1,0 +1,142 @@
+/*
+ * mrlt.h -- C-ABI of the GB300 (sm_103a) library for adaptive cell-average
+ * multiresolution finite volumes with local time-stepping by natural
+ * continuous extension of Runge-Kutta methods (MRLT/NERK), after Lopes,
+ * Domingues, Schneider and Mendes, "Local time-stepping for adaptive
+ * multiresolution using natural extension of Runge-Kutta methods".
+ *
+ * One solver instance = one initial-value problem dq/dt = -div F(q) + S(q)
+ * (Sec. 2, Eq. 1) on a box in d = 1, 2, 3 dimensions, discretised by finite
+ * volumes (Eq. 2) on a dynamically adapted graded tree of nested dyadic grids
+ * (Sec. 2) and advanced in time with compact RK2/RK3 stages (Sec. 3) either
+ * with one global step (MR/RK) or with level-dependent steps dt_l = 2^{L-l} dt
+ * (Eq. 13) synchronised through NERK values (Sec. 4, Algs. 3-9).
+ *
+ * Conventions for every call:
+ *  - The solver owns all of its device memory; it is allocated by mr_create
+ *    and released by mr_destroy.  Host buffers passed in are owned by the
+ *    caller and only read/written during the call.
+ *  - All device work is enqueued on the CUDA stream given to mr_create
+ *    (NULL = legacy default stream).  Every call returns after its work has
+ *    completed on that stream, except where stated.
+ *  - Errors are returned as mr_status; no call aborts the process.  After an
+ *    error, mr_last_error(h) gives a human-readable reason.  MR_E_CUDA means
+ *    a CUDA runtime call failed; the handle should then be destroyed.
+ *  - Not thread-safe per handle; distinct handles are independent.
+ */
+#ifndef MRLT_H
+#define MRLT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mr_solver mr_solver; /* opaque */
+
+typedef enum {
+    MR_OK = 0,
+    MR_E_INVALID = 1, /* bad argument or configuration                    */
+    MR_E_NOMEM = 2,   /* device or host allocation failed                 */
+    MR_E_CUDA = 3,    /* a CUDA runtime call failed                       */
+    MR_E_TIMEOUT = 4, /* reserved: a bounded device wait gave up          */
+    MR_E_STATE = 5,   /* call not valid in the current state, or the tree
+                         invariant was found broken on the device          */
+    MR_E_NUMERIC = 6  /* a non-finite value appeared in the solution       */
+} mr_status;
+
+enum { MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_EULER = 2, MR_EQ_REACTION_DIFFUSION = 3 };
+enum { MR_BC_PERIODIC = 0, MR_BC_NEUMANN = 1 };
+enum { MR_TIME_GTS = 0, MR_TIME_LT_NERK = 1 };
+enum { MR_ADAPT_NEVER = 0, MR_ADAPT_MACRO = 1, MR_ADAPT_EVERY = 2 };
+
+/* Problem statement (Sec. 2, Eq. 1) and the method's parameters. */
+typedef struct mr_config {
+    int    dim;        /* d = 1, 2, 3                                               */
+    int    equation;   /* MR_EQ_*: advection (centred flux, Sec. 4.5), inviscid
+                          Burgers (MUSCL-minmod + Godunov), compressible Euler
+                          (MUSCL-minmod on primitives + HLL), reaction-diffusion
+                          u_t = D lap u + k u (1-u)(u-a) (two-point diffusion)  */
+    int    max_level;  /* L: finest level, 2^L cells per direction (<= 16, d*L <= 30) */
+    int    min_level;  /* coarsest leaf level; one macro step = 2^{L-min} fine steps */
+    double eps;        /* threshold epsilon of Alg. 2; 0 disables coarsening       */
+    int    eps_mode;   /* 0: eps on every level; 1: eps_l = 2^{d (l-L)} eps          */
+    int    rk_order;   /* 2 or 3: compact RK2/RK3 of Sec. 3                          */
+    int    time_mode;  /* MR_TIME_GTS (all leaves step dt) or MR_TIME_LT_NERK       */
+    int    precision;  /* 0 = FP64 (the only value accepted)                        */
+    int    adapt_mode; /* MR_ADAPT_*: never (fixed tree), at each macro-step start,
+                          or at every LT iteration on the synchronised levels      */
+    int    reflux;     /* 1: conservative flux registers at coarse-fine faces (LT)  */
+    double cfl;        /* Courant number sigma                                      */
+    double lo[3], hi[3];/* box [lo, hi] per direction (unused entries ignored)      */
+    int    bc[3];      /* MR_BC_* per direction                                     */
+    double phys[8];    /* advection: a_x, a_y, a_z | Euler: gamma | RD: D, k, a     */
+} mr_config;
+
+/* Create a solver from the finest-level cell averages q0 (host, float64, layout
+ * [var][cell], cell = i + 2^L (j + 2^L k), m = d+2 variables for Euler
+ * (rho, rho u_1..u_d, E), else 1).  The nodes of all levels are formed by
+ * projection (Eq. 3) and, unless adapt_mode == MR_ADAPT_NEVER, the tree is
+ * adapted once (Algs. 1-2).  q0 is read only during the call.
+ * Returns MR_E_INVALID for a bad configuration, MR_E_NOMEM when device memory
+ * is insufficient.  *out receives the handle (NULL on failure). */
+mr_status mr_create(const mr_config* cfg, const double* q0_finest, void* cuda_stream,
+                    mr_solver** out);
+
+/* Re-initialise an existing solver from new finest-level data (same layout as
+ * mr_create): time, counters and tree are reset exactly as mr_create would set
+ * them; no device memory is allocated. */
+mr_status mr_reset(mr_solver* h, const double* q0_finest);
+
+/* Replace the tree by a fixed graded tree given, for every finest cell (host,
+ * uint8, 2^{dL} entries), the level of the leaf that covers it.  Values of the
+ * new leaves are projections or predictions of the current ones (Sec. 2).
+ * MR_E_INVALID if the map is not a graded partition into leaves.
+ * Only allowed at a macro-step boundary. */
+mr_status mr_set_tree(mr_solver* h, const unsigned char* leaf_level_finest);
+
+/* Full adaptation (Algs. 1-2) at the current synchronised time. */
+mr_status mr_adapt(mr_solver* h);
+
+/* Advance to t_target in whole macro steps of 2^{L-min} fine iterations; the
+ * fine step follows the CFL rule once per macro step and the last macro step
+ * is shortened to end exactly at t_target.  Must start at a macro-step
+ * boundary.  *iters_out (may be NULL) receives the fine iterations done. */
+mr_status mr_step(mr_solver* h, double t_target, long long* iters_out);
+
+/* Run n_iters fine iterations (Alg. 3 in LT mode) with the given fine step dt.
+ * May stop inside a macro step; dt may change only at a macro-step boundary. */
+mr_status mr_iterate(mr_solver* h, double dt, long long n_iters, long long* iters_out);
+
+/* What mr_read returns. */
+enum {
+    MR_READ_LEAF_KEYS = 0,   /* int32 [n_leaves][4]: level, i, j, k (ordered by
+                                level, then cell index)                        */
+    MR_READ_LEAF_VALUES = 1, /* double [n_leaves][m], same order, values at the
+                                end of each leaf's latest step                 */
+    MR_READ_UNIFORM = 2,     /* double [m][2^{dL}]: the adapted solution rebuilt
+                                on the finest grid by the inverse MR transform  */
+    MR_READ_STATS = 3        /* double [64]: 0 t, 1 fine iterations, 2 macro steps,
+                                3 dt, 4 leaves, 5 nodes, 6 near-threshold details,
+                                7 leaf updates, 8..12 mass per variable,
+                                15 position in the macro step, 16+l leaves on level l */
+};
+
+/* Copy a result into the caller's host buffer.  With buf == NULL only *used
+ * is set to the size needed; MR_E_INVALID if cap_bytes is too small. */
+mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap_bytes, size_t* used);
+
+/* Release everything owned by the handle (NULL is ignored). */
+void mr_destroy(mr_solver* h);
+
+/* Reason for the last failure on this handle (static string if h is NULL). */
+const char* mr_last_error(const mr_solver* h);
+
+/* Number of kernel launches issued by this handle since creation. */
+long long mr_launch_count(const mr_solver* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

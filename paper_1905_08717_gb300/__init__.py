@@ -1,0 +1,179 @@
+"""GB300-native MRLT/NERK: adaptive multiresolution finite volumes with local
+time-stepping by natural continuous extension of Runge-Kutta methods.
+
+Thin Python binding of the C-ABI in include/mrlt.h (argument marshalling
+only; every step of the method runs in the CUDA library libmrlt.so).  The
+binding raises if the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded synthetic initial data)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "csrc", "libmrlt.so")
+
+MR_READ_LEAF_KEYS, MR_READ_LEAF_VALUES, MR_READ_UNIFORM, MR_READ_STATS = 0, 1, 2, 3
+STATUS = {0: "MR_OK", 1: "MR_E_INVALID", 2: "MR_E_NOMEM", 3: "MR_E_CUDA",
+          4: "MR_E_TIMEOUT", 5: "MR_E_STATE", 6: "MR_E_NUMERIC"}
+
+
+class MRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mr_config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("equation", ctypes.c_int),
+                ("max_level", ctypes.c_int), ("min_level", ctypes.c_int),
+                ("eps", ctypes.c_double), ("eps_mode", ctypes.c_int),
+                ("rk_order", ctypes.c_int), ("time_mode", ctypes.c_int),
+                ("precision", ctypes.c_int), ("adapt_mode", ctypes.c_int),
+                ("reflux", ctypes.c_int), ("cfl", ctypes.c_double),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("bc", ctypes.c_int * 3), ("phys", ctypes.c_double * 8)]
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Load libmrlt.so (raises if it is missing: build it first)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} "
+                               "(run `python -m paper_1905_08717_gb300.build`)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, ll = ctypes.c_void_p, ctypes.c_longlong
+        lib.mr_create.argtypes = [ctypes.POINTER(mr_config), ctypes.POINTER(ctypes.c_double), vp,
+                                  ctypes.POINTER(vp)]
+        lib.mr_reset.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.mr_set_tree.argtypes = [vp, ctypes.POINTER(ctypes.c_ubyte)]
+        lib.mr_adapt.argtypes = [vp]
+        lib.mr_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ll)]
+        lib.mr_iterate.argtypes = [vp, ctypes.c_double, ll, ctypes.POINTER(ll)]
+        lib.mr_read.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        lib.mr_destroy.argtypes = [vp]
+        lib.mr_last_error.argtypes = [vp]
+        lib.mr_last_error.restype = ctypes.c_char_p
+        lib.mr_launch_count.argtypes = [vp]
+        lib.mr_launch_count.restype = ll
+        for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
+                     "mr_iterate", "mr_read"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def make_config(p) -> mr_config:
+    c = mr_config()
+    c.dim, c.equation, c.max_level, c.min_level = p.dim, p.equation, p.max_level, p.min_level
+    c.eps, c.eps_mode, c.rk_order, c.time_mode = p.eps, p.eps_mode, p.rk_order, p.time_mode
+    c.precision, c.adapt_mode, c.reflux, c.cfl = p.precision, p.adapt_mode, p.reflux, p.cfl
+    for k in range(3):
+        c.lo[k], c.hi[k], c.bc[k] = p.lo[k], p.hi[k], p.bc[k]
+    for k in range(8):
+        c.phys[k] = p.phys[k]
+    return c
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Solver:
+    """One MR/MRLT solve on the GPU (handle of the C-ABI `mr_solver`)."""
+
+    def __init__(self, problem, q0: np.ndarray, stream=None):
+        lib = library()
+        self.p = problem
+        self.m = problem.nvars()
+        q = np.ascontiguousarray(q0, dtype=np.float64).reshape(self.m, -1)
+        self._cfg = make_config(problem)
+        self._h = ctypes.c_void_p()
+        r = lib.mr_create(ctypes.byref(self._cfg), _dptr(q), ctypes.c_void_p(_stream_handle(stream)),
+                          ctypes.byref(self._h))
+        if r != 0:
+            raise MRError(r, "mr_create failed")
+
+    def _check(self, r: int, what: str):
+        if r != 0:
+            raise MRError(r, f"{what}: {library().mr_last_error(self._h).decode()}")
+
+    def close(self):
+        if self._h:
+            library().mr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, q0: np.ndarray):
+        q = np.ascontiguousarray(q0, dtype=np.float64).reshape(self.m, -1)
+        self._check(library().mr_reset(self._h, _dptr(q)), "reset")
+
+    def set_tree(self, leaf_level_finest: np.ndarray):
+        a = np.ascontiguousarray(leaf_level_finest, dtype=np.uint8).ravel()
+        self._check(library().mr_set_tree(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))),
+                    "set_tree")
+
+    def adapt(self):
+        self._check(library().mr_adapt(self._h), "adapt")
+
+    def step(self, t_target: float) -> int:
+        it = ctypes.c_longlong()
+        self._check(library().mr_step(self._h, t_target, ctypes.byref(it)), "step")
+        return it.value
+
+    def iterate(self, dt: float, n_iters: int) -> int:
+        it = ctypes.c_longlong()
+        self._check(library().mr_iterate(self._h, dt, n_iters, ctypes.byref(it)), "iterate")
+        return it.value
+
+    def _read(self, what, dtype, shape=None, out=None):
+        lib = library()
+        used = ctypes.c_size_t()
+        self._check(lib.mr_read(self._h, what, None, 0, ctypes.byref(used)), "read size")
+        n = used.value // np.dtype(dtype).itemsize
+        buf = out if out is not None else np.empty(n, dtype=dtype)
+        self._check(lib.mr_read(self._h, what, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes,
+                                ctypes.byref(used)), "read")
+        return buf if shape is None else buf.reshape(shape)
+
+    def leaves(self):
+        k = self._read(MR_READ_LEAF_KEYS, np.int32, (-1, 4))
+        v = self._read(MR_READ_LEAF_VALUES, np.float64, (-1, self.m))
+        return k, v
+
+    def uniform(self) -> np.ndarray:
+        n = 1 << self.p.max_level
+        return self._read(MR_READ_UNIFORM, np.float64, (self.m,) + (n,) * self.p.dim)
+
+    def stats(self) -> dict:
+        s = self._read(MR_READ_STATS, np.float64)
+        L = self.p.max_level
+        return {"t": s[0], "iters": int(s[1]), "macros": int(s[2]), "dt": s[3],
+                "leaves": int(s[4]), "nodes": int(s[5]), "near": int(s[6]),
+                "updates": int(s[7]), "pos": int(s[15]), "mass": s[8:8 + self.m].copy(),
+                "leaves_per_level": s[16:17 + L].astype(np.int64)}
+
+    def launch_count(self) -> int:
+        return int(library().mr_launch_count(self._h))

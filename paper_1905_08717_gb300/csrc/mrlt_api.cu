@@ -1,0 +1,560 @@
+// mrlt_api.cu -- host side of the C-ABI declared in include/mrlt.h: memory
+// layout, the LT iteration schedule (Alg. 3), the global-step MR iteration,
+// macro steps with the CFL rule, and read-back.
+#include "mrlt.h"
+#include "mrlt_tree.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace mrlt;
+
+struct mr_solver {
+    mr_config cfg{};
+    Launcher K;
+    cudaStream_t stream = nullptr;
+    std::vector<void*> allocs;
+    double* d_part = nullptr;
+    double* d_T = nullptr;
+    uint8_t* d_us = nullptr;
+    int* d_keys = nullptr;
+    long long ntot = 0;
+    double t = 0.0, dt = 0.0;
+    long long iters = 0, macros = 0, pos = 0, stage_launches = 0;
+    bool reg = false;
+    std::string err;
+};
+
+namespace {
+
+const char* kNullErr = "null handle";
+
+#define MR_CK(call)                                                               \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return MR_E_CUDA;                                                     \
+        }                                                                         \
+    } while (0)
+
+#define MR_TRY(expr)                 \
+    do {                             \
+        mr_status r_ = (expr);       \
+        if (r_ != MR_OK) return r_;  \
+    } while (0)
+
+mr_status validate(const mr_config* c)
+{
+    if (!c) return MR_E_INVALID;
+    if (c->dim < 1 || c->dim > 3) return MR_E_INVALID;
+    if (c->max_level < 1 || c->max_level > LMAX || c->dim * c->max_level > 30) return MR_E_INVALID;
+    if (c->min_level < 0 || c->min_level > c->max_level) return MR_E_INVALID;
+    if (c->equation < 0 || c->equation > 3) return MR_E_INVALID;
+    if (c->rk_order != 2 && c->rk_order != 3) return MR_E_INVALID;
+    if (c->time_mode != MR_TIME_GTS && c->time_mode != MR_TIME_LT_NERK) return MR_E_INVALID;
+    if (c->precision != 0) return MR_E_INVALID;
+    if (c->adapt_mode < 0 || c->adapt_mode > 2) return MR_E_INVALID;
+    if (!(c->cfl > 0.0) || !(c->eps >= 0.0)) return MR_E_INVALID;
+    for (int k = 0; k < c->dim; ++k) {
+        if (!(c->hi[k] > c->lo[k])) return MR_E_INVALID;
+        if (c->bc[k] != MR_BC_PERIODIC && c->bc[k] != MR_BC_NEUMANN) return MR_E_INVALID;
+    }
+    if (c->equation == MR_EQ_EULER && !(c->phys[0] > 1.0)) return MR_E_INVALID;
+    return MR_OK;
+}
+
+template <class T>
+mr_status dev_alloc(mr_solver* h, T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return MR_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        *p = nullptr;
+        cudaGetLastError();
+        return MR_E_NOMEM;
+    }
+    h->allocs.push_back(*p);
+    return MR_OK;
+}
+
+int level_min(const mr_solver* h, long long n)
+{
+    const Grid& g = h->K.g;
+    for (int l = g.lb; l <= g.L; ++l)
+        if (n % (1LL << (g.L - l)) == 0) return l;
+    return g.L;
+}
+
+void stage(mr_solver* h, int u, int s, int lmin, double dtl)
+{
+    const Grid& g = h->K.g;
+    static const double b2[2] = {0.5, 0.5};
+    static const double b3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+    const double b = g.rk == 2 ? b2[s - 1] : b3[s - 1];
+    const int reg = h->reg && !g.gts;
+    launch_stage(g, h->stream, u, s, lmin, dtl, dtl * b, reg);
+    ++h->stage_launches;
+}
+
+mr_status sync_check(mr_solver* h)
+{
+    MR_CK(cudaGetLastError());
+    MR_CK(cudaStreamSynchronize(h->stream));
+    int e = 0;
+    MR_CK(cudaMemcpy(&e, h->K.g.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "device reported error bits 0x%x", e);
+        h->err = buf;
+        return (e & ERR_NONFINITE) ? MR_E_NUMERIC : MR_E_STATE;
+    }
+    return MR_OK;
+}
+
+// Algs. 1-2 restricted to levels >= la (full adaptation for la = min_level)
+mr_status adapt(mr_solver* h, int la)
+{
+    Grid& g = h->K.g;
+    if (la >= g.L) return MR_OK;
+    if (la == g.lb) {
+        unsigned long long init[MMAX];
+        const double tiny = 1e-14;
+        for (int v = 0; v < MMAX; ++v) memcpy(&init[v], &tiny, sizeof tiny);
+        MR_CK(cudaMemcpyAsync(g.scale_bits, init, sizeof init, cudaMemcpyHostToDevice, h->stream));
+        for (int l = g.lb; l <= g.L; ++l) h->K.scale(l);
+    }
+    MR_CK(cudaMemsetAsync(g.flag + g.off[la], 0, (size_t)(h->ntot - g.off[la]), h->stream));
+    h->K.mark_refinements(la);
+    h->K.apply_tree(la);
+    for (int l = la; l <= g.L; ++l) h->K.compact(l);
+    for (int l = g.L - 1; l >= la; --l) h->K.project(l, PM_Q0);
+    return MR_OK;
+}
+
+// one iteration n (0-based in the macro step) of Alg. 3
+mr_status lt_iteration(mr_solver* h, long long n, long long nit)
+{
+    Grid& g = h->K.g;
+    const int L = g.L, lb = g.lb, lmin = level_min(h, n);
+    const double dt = h->dt;
+    for (int l = lmin; l <= L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_Q0);
+    if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
+        MR_TRY(adapt(h, lmin));
+    if (lmin > lb) h->K.project(lmin - 1, PM_MID);
+    for (int l = L; l >= lmin; --l) stage(h, l, 1, lmin, ldexp(dt, L - l));
+    for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF2);
+    for (int l = L; l >= lmin; --l) {
+        if (l < L) h->K.project(l, PM_PRJ2);
+        stage(h, l, 2, lmin, ldexp(dt, L - l));
+    }
+    if (g.rk == 3) {
+        for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF3);
+        for (int l = L; l >= lmin; --l) {
+            if (l < L) h->K.project(l, PM_PRJ3);
+            stage(h, l, 3, lmin, ldexp(dt, L - l));
+        }
+    }
+    if (h->reg) {
+        const int lc = (n + 1 == nit) ? lb : level_min(h, n + 1);
+        for (int l = lc; l < L; ++l) h->K.reflux(l);
+    }
+    return MR_OK;
+}
+
+// global time step MR (MR/RK2, MR/RK3)
+mr_status gts_iteration(mr_solver* h, long long n)
+{
+    Grid& g = h->K.g;
+    const int L = g.L, lb = g.lb;
+    for (int l = lb; l <= L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
+    if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
+        MR_TRY(adapt(h, lb));
+    for (int l = L; l >= lb; --l) stage(h, l, 1, lb, h->dt);
+    for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q1);
+    for (int l = L; l >= lb; --l) stage(h, l, 2, lb, h->dt);
+    if (g.rk == 3) {
+        for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q2);
+        for (int l = L; l >= lb; --l) stage(h, l, 3, lb, h->dt);
+    }
+    return MR_OK;
+}
+
+mr_status finite_check(mr_solver* h)
+{
+    for (int l = h->K.g.lb; l <= h->K.g.L; ++l) h->K.finite(l);
+    return sync_check(h);
+}
+
+mr_status run_iters(mr_solver* h, double dt, long long n)
+{
+    const long long nit = 1LL << (h->K.g.L - h->K.g.lb);
+    if (h->pos != 0 && dt != h->dt) {
+        h->err = "dt changed inside a macro step";
+        return MR_E_STATE;
+    }
+    h->dt = dt;
+    for (long long i = 0; i < n; ++i) {
+        if (h->K.g.gts) MR_TRY(gts_iteration(h, h->pos));
+        else MR_TRY(lt_iteration(h, h->pos, nit));
+        ++h->iters;
+        ++h->pos;
+        if (h->pos == nit) {
+            h->pos = 0;
+            ++h->macros;
+            MR_TRY(finite_check(h));
+        }
+    }
+    return MR_OK;
+}
+
+// CFL step of the finest level: sigma * min(dx_L / max sum_k lambda_k, dx_L^2 / (2 d D))
+mr_status cfl_dt(mr_solver* h, double* dt)
+{
+    Grid& g = h->K.g;
+    MR_CK(cudaMemsetAsync(g.wmax, 0, sizeof(unsigned long long), h->stream));
+    for (int l = g.lb; l <= g.L; ++l) {
+        launch_wave(g, h->stream, l);
+        ++h->stage_launches;
+    }
+    unsigned long long bits = 0;
+    MR_CK(cudaMemcpyAsync(&bits, g.wmax, sizeof bits, cudaMemcpyDeviceToHost, h->stream));
+    MR_TRY(sync_check(h));
+    double lam;
+    memcpy(&lam, &bits, sizeof lam);
+    double dxm = g.dx[g.L][0];
+    for (int k = 1; k < g.d; ++k) dxm = fmin(dxm, g.dx[g.L][k]);
+    double d = lam > 0.0 ? dxm / lam : dxm;
+    if (g.eq == MR_EQ_REACTION_DIFFUSION) {
+        const double dd = dxm * dxm / (2.0 * g.d * g.phys[0]);
+        if (lam <= 0.0 || dd < d) d = dd;
+    }
+    *dt = h->cfg.cfl * d;
+    return MR_OK;
+}
+
+mr_status init_state(mr_solver* h, const double* q0)
+{
+    Grid& g = h->K.g;
+    const int m = g.m;
+    const size_t nd = (size_t)h->ntot * m;
+    for (int f = 0; f < NFIELD; ++f) MR_CK(cudaMemsetAsync(g.f[f], 0, nd * sizeof(double), h->stream));
+    if (g.rc) {
+        MR_CK(cudaMemsetAsync(g.rc, 0, nd * g.nf * sizeof(double), h->stream));
+        MR_CK(cudaMemsetAsync(g.rf, 0, nd * g.nf * sizeof(double), h->stream));
+    }
+    MR_CK(cudaMemsetAsync(g.flag, 0, h->ntot, h->stream));
+    MR_CK(cudaMemsetAsync(g.counts, 0, 2 * (LMAX + 1) * sizeof(int), h->stream));
+    MR_CK(cudaMemsetAsync(g.err, 0, sizeof(int), h->stream));
+    MR_CK(cudaMemsetAsync(g.near, 0, sizeof(unsigned long long), h->stream));
+    MR_CK(cudaMemsetAsync(g.updates, 0, sizeof(unsigned long long), h->stream));
+    MR_CK(cudaMemcpyAsync(g.f[F_Q0] + g.off[g.L] * m, q0, (size_t)g.N[g.L] * m * sizeof(double),
+                          cudaMemcpyHostToDevice, h->stream));
+    for (int l = g.lb; l <= g.L; ++l)
+        MR_CK(cudaMemsetAsync(g.st + g.off[l], l < g.L ? 2 : 1, (size_t)g.N[l], h->stream));
+    for (int l = g.lb; l <= g.L; ++l) h->K.compact(l);
+    for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
+    if (h->cfg.adapt_mode != MR_ADAPT_NEVER) MR_TRY(adapt(h, g.lb));
+    for (int l = g.lb; l <= g.L; ++l) h->K.leaf_copy(l, F_Q0, F_QE);
+    h->t = h->dt = 0.0;
+    h->iters = h->macros = h->pos = 0;
+    return sync_check(h);
+}
+
+} // namespace
+
+extern "C" {
+
+mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, mr_solver** out)
+{
+    if (!out) return MR_E_INVALID;
+    *out = nullptr;
+    if (validate(cfg) != MR_OK || !q0) return MR_E_INVALID;
+    mr_solver* h = new (std::nothrow) mr_solver();
+    if (!h) return MR_E_NOMEM;
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->K.st = h->stream;
+    Grid& g = h->K.g;
+    memset(&g, 0, sizeof g);
+    g.d = cfg->dim;
+    g.m = cfg->equation == MR_EQ_EULER ? cfg->dim + 2 : 1;
+    g.nf = 2 * g.d;
+    g.L = cfg->max_level;
+    g.lb = cfg->min_level;
+    g.eq = cfg->equation;
+    g.rk = cfg->rk_order;
+    g.gts = cfg->time_mode == MR_TIME_GTS;
+    for (int k = 0; k < 3; ++k) g.bc[k] = cfg->bc[k];
+    for (int k = 0; k < 8; ++k) g.phys[k] = cfg->phys[k];
+    g.eps = cfg->eps;
+    g.eps_mode = cfg->eps_mode;
+    long long off = 0;
+    for (int l = g.lb; l <= g.L; ++l) {
+        g.off[l] = off;
+        g.N[l] = 1LL << (g.d * l);
+        g.n[l] = 1 << l;
+        for (int k = 0; k < 3; ++k) g.dx[l][k] = (cfg->hi[k] - cfg->lo[k]) / g.n[l];
+        off += g.N[l];
+    }
+    h->ntot = off;
+    h->reg = cfg->reflux && !g.gts;
+    const size_t nd = (size_t)off * g.m;
+    mr_status r = MR_OK;
+    auto A = [&](mr_status s) {
+        if (r == MR_OK) r = s;
+    };
+    A(dev_alloc(h, &g.st, off));
+    A(dev_alloc(h, &g.flag, off));
+    for (int f = 0; f < NFIELD; ++f) A(dev_alloc(h, &g.f[f], nd));
+    if (h->reg) {
+        A(dev_alloc(h, &g.rc, nd * g.nf));
+        A(dev_alloc(h, &g.rf, nd * g.nf));
+    }
+    A(dev_alloc(h, &g.leaves, off));
+    A(dev_alloc(h, &g.inner, off));
+    A(dev_alloc(h, &g.counts, 2 * (LMAX + 1)));
+    A(dev_alloc(h, &g.scale_bits, MMAX));
+    A(dev_alloc(h, &g.err, 1));
+    A(dev_alloc(h, &g.near, 1));
+    A(dev_alloc(h, &g.wmax, 1));
+    A(dev_alloc(h, &g.updates, 1));
+    A(dev_alloc(h, &h->K.bc, 2 * ((g.N[g.L] + NTHREADS - 1) / NTHREADS)));
+    A(dev_alloc(h, &h->d_part, (size_t)(LMAX + 1) * MASS_BLOCKS * g.m));
+    A(dev_alloc(h, &h->d_T, nd));
+    A(dev_alloc(h, &h->d_us, off));
+    A(dev_alloc(h, &h->d_keys, off * 4));
+    if (r == MR_OK) r = init_state(h, q0);
+    if (r != MR_OK) {
+        fprintf(stderr, "mr_create: %s\n", h->err.c_str());
+        mr_destroy(h);
+        return r;
+    }
+    *out = h;
+    return MR_OK;
+}
+
+mr_status mr_reset(mr_solver* h, const double* q0)
+{
+    if (!h || !q0) return MR_E_INVALID;
+    return init_state(h, q0);
+}
+
+mr_status mr_set_tree(mr_solver* h, const unsigned char* lev)
+{
+    if (!h || !lev) return MR_E_INVALID;
+    if (h->pos != 0) return MR_E_STATE;
+    Grid& g = h->K.g;
+    const int L = g.L, lb = g.lb, d = g.d;
+    std::vector<std::vector<uint8_t>> R(L + 1);
+    for (int l = lb; l <= L; ++l) R[l].assign((size_t)g.N[l], 0);
+    const long long NL = g.N[L], nL = g.n[L];
+    auto coords = [&](int l, long long id, int c[3]) {
+        const long long n = g.n[l];
+        c[0] = (int)(id % n);
+        c[1] = d > 1 ? (int)((id / n) % n) : 0;
+        c[2] = d > 2 ? (int)(id / (n * n)) : 0;
+    };
+    auto lid = [&](int l, const int c[3]) {
+        const long long n = g.n[l];
+        return (long long)c[0] + n * ((long long)c[1] + n * (long long)c[2]);
+    };
+    (void)nL;
+    for (long long id = 0; id < NL; ++id) {
+        if (lev[id] < lb || lev[id] > L) {
+            h->err = "set_tree: level out of range";
+            return MR_E_INVALID;
+        }
+        int c[3];
+        coords(L, id, c);
+        for (int l = lb; l < lev[id]; ++l) {
+            int p[3] = {c[0] >> (L - l), d > 1 ? c[1] >> (L - l) : 0, d > 2 ? c[2] >> (L - l) : 0};
+            R[l][lid(l, p)] = 1;
+        }
+    }
+    for (long long id = 0; id < NL; ++id) { // leaves partition the box as the map says
+        int c[3];
+        coords(L, id, c);
+        int lv = lb;
+        for (int l = lb; l < L; ++l) {
+            int p[3] = {c[0] >> (L - l), d > 1 ? c[1] >> (L - l) : 0, d > 2 ? c[2] >> (L - l) : 0};
+            if (!R[l][lid(l, p)]) break;
+            lv = l + 1;
+        }
+        if (lv != lev[id]) {
+            h->err = "set_tree: map is not a leaf partition";
+            return MR_E_INVALID;
+        }
+    }
+    for (int l = L - 1; l > lb; --l) // graded
+        for (long long id = 0; id < g.N[l]; ++id) {
+            if (!R[l][id]) continue;
+            int c[3];
+            coords(l, id, c);
+            const int P[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
+            for (int dz = (d > 2 ? -1 : 0); dz <= (d > 2 ? 1 : 0); ++dz)
+                for (int dy = (d > 1 ? -1 : 0); dy <= (d > 1 ? 1 : 0); ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int off3[3] = {dx, dy, dz};
+                        int q[3] = {0, 0, 0};
+                        bool ok = true;
+                        for (int k = 0; k < d; ++k) {
+                            int p = P[k] + off3[k], n = g.n[l - 1];
+                            if (g.bc[k] == MR_BC_PERIODIC) p = ((p % n) + n) % n;
+                            else if (p < 0 || p >= n) ok = false;
+                            q[k] = p;
+                        }
+                        if (ok && !R[l - 1][lid(l - 1, q)]) {
+                            h->err = "set_tree: map is not graded";
+                            return MR_E_INVALID;
+                        }
+                    }
+        }
+    for (int l = lb; l <= L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
+    MR_CK(cudaMemsetAsync(g.flag, 0, h->ntot, h->stream));
+    std::vector<uint8_t> fl((size_t)h->ntot, 0);
+    for (int l = lb; l < L; ++l)
+        for (long long id = 0; id < g.N[l]; ++id)
+            if (R[l][id]) fl[g.off[l] + id] = FL_REF;
+    MR_CK(cudaMemcpyAsync(g.flag, fl.data(), fl.size(), cudaMemcpyHostToDevice, h->stream));
+    h->K.apply_tree(lb);
+    for (int l = lb; l <= L; ++l) h->K.compact(l);
+    for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
+    for (int l = lb; l <= L; ++l) h->K.leaf_copy(l, F_Q0, F_QE);
+    return sync_check(h);
+}
+
+mr_status mr_adapt(mr_solver* h)
+{
+    if (!h) return MR_E_INVALID;
+    if (h->pos != 0) return MR_E_STATE;
+    Grid& g = h->K.g;
+    for (int l = g.lb; l <= g.L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
+    MR_TRY(adapt(h, g.lb));
+    for (int l = g.lb; l <= g.L; ++l) h->K.leaf_copy(l, F_Q0, F_QE);
+    return sync_check(h);
+}
+
+mr_status mr_step(mr_solver* h, double t_target, long long* iters_out)
+{
+    if (!h) return MR_E_INVALID;
+    if (h->pos != 0) return MR_E_STATE;
+    const long long it0 = h->iters, nit = 1LL << (h->K.g.L - h->K.g.lb);
+    while (h->t < t_target) {
+        double dt;
+        MR_TRY(cfl_dt(h, &dt));
+        bool last = false;
+        if (h->t + nit * dt >= t_target * (1.0 - 1e-14)) {
+            dt = (t_target - h->t) / nit;
+            last = true;
+        }
+        const double t0 = h->t;
+        MR_TRY(run_iters(h, dt, nit));
+        h->t = last ? t_target : t0 + nit * dt;
+    }
+    if (iters_out) *iters_out = h->iters - it0;
+    return sync_check(h);
+}
+
+mr_status mr_iterate(mr_solver* h, double dt, long long n, long long* iters_out)
+{
+    if (!h || !(dt > 0.0) || n < 0) return MR_E_INVALID;
+    const long long it0 = h->iters;
+    for (long long i = 0; i < n; ++i) {
+        MR_TRY(run_iters(h, dt, 1));
+        h->t += dt;
+    }
+    if (iters_out) *iters_out = h->iters - it0;
+    return sync_check(h);
+}
+
+mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
+{
+    if (!h) return MR_E_INVALID;
+    Grid& g = h->K.g;
+    const int m = g.m;
+    int cnt[2 * (LMAX + 1)];
+    MR_CK(cudaMemcpyAsync(cnt, g.counts, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaStreamSynchronize(h->stream));
+    long long nleaf = 0, nnode = 0;
+    for (int l = g.lb; l <= g.L; ++l) {
+        nleaf += cnt[l];
+        nnode += cnt[l] + cnt[LMAX + 1 + l];
+    }
+    size_t need;
+    if (what == MR_READ_LEAF_KEYS) need = (size_t)nleaf * 4 * sizeof(int);
+    else if (what == MR_READ_LEAF_VALUES) need = (size_t)nleaf * m * sizeof(double);
+    else if (what == MR_READ_UNIFORM) need = (size_t)g.N[g.L] * m * sizeof(double);
+    else if (what == MR_READ_STATS) need = 64 * sizeof(double);
+    else return MR_E_INVALID;
+    if (used) *used = need;
+    if (!buf) return MR_OK;
+    if (cap < need) return MR_E_INVALID;
+    if (what == MR_READ_LEAF_KEYS || what == MR_READ_LEAF_VALUES) {
+        long long base = 0;
+        for (int l = g.lb; l <= g.L; ++l) {
+            if (cnt[l]) h->K.pack(l, base, what == MR_READ_LEAF_KEYS ? h->d_keys : nullptr,
+                                  what == MR_READ_LEAF_VALUES ? h->d_T : nullptr);
+            base += cnt[l];
+        }
+        const void* src = what == MR_READ_LEAF_KEYS ? (const void*)h->d_keys : (const void*)h->d_T;
+        if (need) MR_CK(cudaMemcpyAsync(buf, src, need, cudaMemcpyDeviceToHost, h->stream));
+    } else if (what == MR_READ_UNIFORM) {
+        h->K.uniform(h->d_T, h->d_us);
+        MR_CK(cudaMemcpyAsync(buf, h->d_T + g.off[g.L] * m, need, cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        double* S = (double*)buf;
+        memset(S, 0, 64 * sizeof(double));
+        std::vector<double> part((size_t)(LMAX + 1) * MASS_BLOCKS * m, 0.0);
+        for (int l = g.lb; l <= g.L; ++l) h->K.mass(l, h->d_part + (size_t)l * MASS_BLOCKS * m);
+        MR_CK(cudaMemcpyAsync(part.data(), h->d_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+        unsigned long long near = 0, upd = 0;
+        MR_CK(cudaMemcpyAsync(&near, g.near, sizeof near, cudaMemcpyDeviceToHost, h->stream));
+        MR_CK(cudaMemcpyAsync(&upd, g.updates, sizeof upd, cudaMemcpyDeviceToHost, h->stream));
+        MR_CK(cudaStreamSynchronize(h->stream));
+        S[0] = h->t;
+        S[1] = (double)h->iters;
+        S[2] = (double)h->macros;
+        S[3] = h->dt;
+        S[4] = (double)nleaf;
+        S[5] = (double)nnode;
+        S[6] = (double)near;
+        S[7] = (double)upd;
+        S[15] = (double)h->pos;
+        for (int l = g.lb; l <= g.L; ++l) {
+            S[16 + l] = cnt[l];
+            double vol = 1.0;
+            for (int k = 0; k < g.d; ++k) vol *= g.dx[l][k];
+            for (int v = 0; v < m; ++v) {
+                double s = 0.0;
+                for (int b = 0; b < MASS_BLOCKS; ++b) s += part[((size_t)l * MASS_BLOCKS + b) * m + v];
+                S[8 + v] += s * vol;
+            }
+        }
+    }
+    return sync_check(h);
+}
+
+void mr_destroy(mr_solver* h)
+{
+    if (!h) return;
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+const char* mr_last_error(const mr_solver* h) { return h ? h->err.c_str() : kNullErr; }
+
+long long mr_launch_count(const mr_solver* h) { return h ? h->K.n + h->stage_launches : 0; }
+
+} // extern "C"

@@ -1,0 +1,412 @@
+// mrlt_impl.cuh -- device data layout and shared device routines of the
+// MRLT/NERK library (private to the library; the public C-ABI is mrlt.h).
+//
+// Data layout in HBM (one solver instance):
+//   every level l in [min_level, L] is a dense grid of N_l = 2^{d l} cells,
+//   cell id = i + n_l (j + n_l k), n_l = 2^l.  All levels of one quantity
+//   live in one "pyramid" allocation at offset off[l] (cells).
+//   - status pyramid (uint8): 0 absent, 1 leaf, 2 internal node
+//   - field pyramids (float64, SoA per level: [off_l * m + v * N_l + id]):
+//       Q0 q^n, Q1 q*, Q2 q**, QE q^{n+1} (leaves: compact RK stages of Sec. 3;
+//       internal nodes: the projections / refreshed values of Algs. 3-9),
+//       XH half-step value (Eq. 17), NH, N1, N3 the NERK theta = 1/2, 1/4, 3/4
+//       values of internal nodes.  Leaves never store NERK values: they are
+//       recomputed from Q0, Q1, Q2, QE where needed (same polynomial).
+//   - register pyramids (float64, [off_l * nf * m + (face * m + v) * N_l + id]):
+//       coarse-side (RC) and fine-side (RF) time-integrated face fluxes.
+//   - per-level compact lists (int32) of leaves and internal nodes, ascending
+//     cell id, rebuilt after every remesh by warp-ballot stream compaction.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mrlt {
+
+constexpr int LMAX = 16;
+constexpr int MMAX = 5;
+constexpr int NTHREADS = 128;
+
+enum Field { F_Q0 = 0, F_Q1, F_Q2, F_QE, F_XH, F_NH, F_N1, F_N3, NFIELD };
+enum Kind { K_WALL = 0, K_LEAF = 1, K_FINER = 2, K_COARSER = 3 };
+enum FlagBits { FL_SIG = 1, FL_BIG = 2, FL_DES = 4, FL_ALLOW = 8, FL_REF = 16 };
+enum ErrBits { ERR_INDEX = 1, ERR_SOURCE = 2, ERR_NONFINITE = 4, ERR_REFLUX = 8 };
+
+struct Grid {
+    uint8_t* st;
+    uint8_t* flag;
+    double* f[NFIELD];
+    double* rc;
+    double* rf;
+    int* leaves;
+    int* inner;
+    int* counts;                    // [0..LMAX] leaves, [LMAX+1..] internal nodes
+    double* scale;                  // [MMAX] detail normalisation s_v
+    unsigned long long* scale_bits; // [MMAX] running max |q_v| (bit pattern)
+    int* err;
+    unsigned long long* near;
+    unsigned long long* wmax;
+    unsigned long long* updates;
+    long long off[LMAX + 1];
+    long long N[LMAX + 1];
+    int n[LMAX + 1];
+    double dx[LMAX + 1][3];
+    int d, m, nf, L, lb, eq, rk, gts;
+    int bc[3];
+    double phys[8];
+    double eps;
+    int eps_mode;
+};
+
+// exposure context: level u being updated, stage s (0 = plain q^n), lmin
+struct Ctx {
+    int u, s, lmin;
+};
+
+__device__ __forceinline__ int wrap_or_mirror(const Grid& g, int l, int k, int p)
+{
+    const int n = g.n[l];
+    if (g.bc[k] == 0) {
+        p %= n;
+        return p < 0 ? p + n : p;
+    }
+#pragma unroll 1
+    for (int it = 0; it < 8 && (p < 0 || p >= n); ++it) {
+        if (p < 0) p = -1 - p;
+        if (p >= n) p = 2 * n - 1 - p;
+    }
+    return p < 0 ? 0 : (p >= n ? n - 1 : p);
+}
+
+// neighbourhood rule of the tree: wrap when periodic, drop cells past a wall
+__device__ __forceinline__ bool in_box(const Grid& g, int l, int k, int p, int* q)
+{
+    const int n = g.n[l];
+    if (g.bc[k] == 0) {
+        p %= n;
+        *q = p < 0 ? p + n : p;
+        return true;
+    }
+    if (p < 0 || p >= n) return false;
+    *q = p;
+    return true;
+}
+
+__device__ __forceinline__ long long cell_id(const Grid& g, int l, int x, int y, int z)
+{
+    const long long n = g.n[l];
+    return (long long)x + n * ((long long)y + n * (long long)z);
+}
+
+__device__ __forceinline__ void cell_xyz(const Grid& g, int l, long long id, int c[3])
+{
+    const long long n = g.n[l];
+    c[0] = (int)(id % n);
+    c[1] = g.d > 1 ? (int)((id / n) % n) : 0;
+    c[2] = g.d > 2 ? (int)(id / (n * n)) : 0;
+}
+
+__device__ __forceinline__ const double* fbase(const Grid& g, int f, int l)
+{
+    return g.f[f] + g.off[l] * g.m;
+}
+__device__ __forceinline__ double* fbase_w(const Grid& g, int f, int l)
+{
+    return g.f[f] + g.off[l] * g.m;
+}
+
+__device__ __forceinline__ uint8_t status(const Grid& g, int l, long long id)
+{
+    return g.st[g.off[l] + id];
+}
+
+// Value of stored node (l, id) (status st) as seen by the stencil of a
+// level-u leaf at stage x.s of the current iteration: the exposure table of
+// Secs. 4.1-4.3 / Algs. 3-9.  Leaves recompute their NERK values from the
+// stage values: with k1 = q* - q^n and k2 the second stage increment
+// (RK2: k2 = 2 q^{n+1} - q^n - q*, RK3: k2 = 4 q** - 3 q^n - q*),
+// q(theta) = q^n + (theta - theta^2/2) k1 + theta^2/2 k2 (Sec. 3 NERK2).
+template <int M>
+__device__ __forceinline__ void expose(const Grid& g, const Ctx& x, int l, long long id, int st,
+                                       double* out)
+{
+    const long long N = g.N[l];
+    const double* q0 = fbase(g, F_Q0, l) + id;
+    const double* q1 = fbase(g, F_Q1, l) + id;
+    const double* q2 = fbase(g, F_Q2, l) + id;
+    const double* qe = fbase(g, F_QE, l) + id;
+    const int s = x.s;
+    const int rel = l - x.u;
+    if (s == 0 || (s == 1 && g.gts) || (s == 1 && (rel >= 0 || l >= x.lmin))) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[v] = q0[v * N];
+        return;
+    }
+    if (g.gts) {
+        const double* a = s == 2 ? q1 : q2;
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[v] = a[v * N];
+        return;
+    }
+    if (s == 1) { // coarser level lmin-1, mid-step: theta = 1/2 value
+        if (g.rk == 3) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = q2[v * N];
+        } else if (st == 1) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = 0.5 * q0[v * N] + 0.25 * q1[v * N] + 0.25 * qe[v * N];
+        } else {
+            const double* nh = fbase(g, F_NH, l) + id;
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = nh[v * N];
+        }
+        return;
+    }
+    if (s == 2) {
+        if (rel == 0) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = q1[v * N];
+        } else if (rel == 1) {
+            if (st == 1) { // Eq. 14: q* + k2
+                if (g.rk == 2) {
+#pragma unroll
+                    for (int v = 0; v < M; ++v) out[v] = 2.0 * qe[v * N] - q0[v * N];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < M; ++v) out[v] = 4.0 * q2[v * N] - 3.0 * q0[v * N];
+                }
+            } else { // Eq. 15
+#pragma unroll
+                for (int v = 0; v < M; ++v) out[v] = 2.0 * q1[v * N] - q0[v * N];
+            }
+        } else if (l >= x.lmin) { // half step of the coarser level
+            if (st == 1) {
+#pragma unroll
+                for (int v = 0; v < M; ++v) out[v] = q0[v * N] + 0.5 * (q1[v * N] - q0[v * N]);
+            } else {
+                const double* xh = fbase(g, F_XH, l) + id;
+#pragma unroll
+                for (int v = 0; v < M; ++v) out[v] = xh[v * N];
+            }
+        } else { // end of the mid-step coarser level
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = qe[v * N];
+        }
+        return;
+    }
+    // stage 3
+    if (rel == 0) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[v] = q2[v * N];
+    } else if (rel == 1) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[v] = qe[v * N];
+    } else {
+        const bool act = l >= x.lmin;
+        if (st == 1) {
+            const double b1 = act ? 7.0 / 32.0 : 15.0 / 32.0;
+            const double b2 = act ? 1.0 / 32.0 : 9.0 / 32.0;
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+                const double a0 = q0[v * N], a1 = q1[v * N];
+                const double k1 = a1 - a0;
+                const double k2 = 4.0 * q2[v * N] - 3.0 * a0 - a1;
+                out[v] = a0 + b1 * k1 + b2 * k2;
+            }
+        } else {
+            const double* nn = fbase(g, act ? F_N1 : F_N3, l) + id;
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = nn[v * N];
+        }
+    }
+}
+
+// 1D prediction weights of Eq. 4 for child offset a (0 left, 1 right):
+// child = parent + s (right - left) / 8, s = -1 for a = 0, +1 for a = 1.
+__device__ __forceinline__ double pw(int a, int delta)
+{
+    if (delta == 0) return 1.0;
+    const double s = a ? 0.125 : -0.125;
+    return delta > 0 ? s : -s;
+}
+
+// Tensor-product prediction (Eq. 4 applied along each direction) of the cell
+// at in-box coordinates q of level l from the 3^d stored nodes of level l-1
+// around its parent, using their exposures.
+template <int D, int M>
+__device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, const int q[3], double* out)
+{
+    const int pl = l - 1;
+#pragma unroll
+    for (int v = 0; v < M; ++v) out[v] = 0.0;
+    if (pl < g.lb) {
+        atomicOr(g.err, ERR_SOURCE);
+        return;
+    }
+    const int P0 = q[0] >> 1, P1 = q[1] >> 1, P2 = q[2] >> 1;
+    const int a0 = q[0] & 1, a1 = q[1] & 1, a2 = q[2] & 1;
+#pragma unroll 1
+    for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
+        const int z = D > 2 ? wrap_or_mirror(g, pl, 2, P2 + dz) : 0;
+        const double wz = D > 2 ? pw(a2, dz) : 1.0;
+#pragma unroll 1
+        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
+            const int y = D > 1 ? wrap_or_mirror(g, pl, 1, P1 + dy) : 0;
+            const double wyz = wz * (D > 1 ? pw(a1, dy) : 1.0);
+#pragma unroll
+            for (int dxx = -1; dxx <= 1; ++dxx) {
+                const int xx = wrap_or_mirror(g, pl, 0, P0 + dxx);
+                const long long id = cell_id(g, pl, xx, y, z);
+                const int st = status(g, pl, id);
+                if (st == 0) {
+                    atomicOr(g.err, ERR_SOURCE);
+                    continue;
+                }
+                double val[M];
+                expose<M>(g, x, pl, id, st, val);
+                const double w = wyz * pw(a0, dxx);
+#pragma unroll
+                for (int v = 0; v < M; ++v) out[v] += w * val[v];
+            }
+        }
+    }
+}
+
+// value of the cell at (possibly out-of-box) coordinates p on level l
+template <int D, int M>
+__device__ __forceinline__ void value_at(const Grid& g, const Ctx& x, int l, const int p[3], double* out)
+{
+    int q[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < D; ++k) q[k] = wrap_or_mirror(g, l, k, p[k]);
+    const long long id = cell_id(g, l, q[0], q[1], q[2]);
+    const int st = status(g, l, id);
+    if (st) expose<M>(g, x, l, id, st, out);
+    else predict<D, M>(g, x, l, q, out);
+}
+
+// ---------------------------------------------------------------- physics
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+// numerical flux along direction k across the face between W[1] and W[2]
+template <int EQ, int D, int M>
+__device__ __forceinline__ void num_flux(const Grid& g, int k, double dxf, const double (&W)[4][M], double* F)
+{
+    if constexpr (EQ == 0) { // linear advection, centred flux
+        F[0] = g.phys[k] * (W[1][0] + W[2][0]) * 0.5;
+    } else if constexpr (EQ == 3) { // two-point diffusive flux
+        F[0] = -g.phys[0] * (W[2][0] - W[1][0]) / dxf;
+    } else if constexpr (EQ == 1) { // Burgers: MUSCL-minmod + Godunov
+        const double uL = W[1][0] + 0.5 * minmod(W[1][0] - W[0][0], W[2][0] - W[1][0]);
+        const double uR = W[2][0] - 0.5 * minmod(W[2][0] - W[1][0], W[3][0] - W[2][0]);
+        const double fL = 0.5 * uL * uL, fR = 0.5 * uR * uR;
+        if (uL <= uR) F[0] = uL > 0.0 ? fL : (uR < 0.0 ? fR : 0.0);
+        else F[0] = fmax(fL, fR);
+    } else { // Euler: MUSCL-minmod on (rho, u_1..u_d, p) + HLL
+        const double gam = g.phys[0];
+        double P[4][M];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double rho = W[i][0];
+            const double ir = 1.0 / rho;
+            double ke = 0.0;
+            P[i][0] = rho;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                P[i][1 + c] = W[i][1 + c] * ir;
+                ke += W[i][1 + c] * P[i][1 + c];
+            }
+            P[i][D + 1] = (gam - 1.0) * (W[i][D + 1] - 0.5 * ke);
+        }
+        double PL[M], PR[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            PL[v] = P[1][v] + 0.5 * minmod(P[1][v] - P[0][v], P[2][v] - P[1][v]);
+            PR[v] = P[2][v] - 0.5 * minmod(P[2][v] - P[1][v], P[3][v] - P[2][v]);
+        }
+        double UL[M], UR[M], FL[M], FR[M];
+        double keL = 0.0, keR = 0.0;
+        UL[0] = PL[0];
+        UR[0] = PR[0];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            UL[1 + c] = PL[0] * PL[1 + c];
+            UR[1 + c] = PR[0] * PR[1 + c];
+            keL += PL[1 + c] * PL[1 + c];
+            keR += PR[1 + c] * PR[1 + c];
+        }
+        const double igm = 1.0 / (gam - 1.0);
+        UL[D + 1] = PL[D + 1] * igm + 0.5 * PL[0] * keL;
+        UR[D + 1] = PR[D + 1] * igm + 0.5 * PR[0] * keR;
+        const double unL = PL[1 + k], unR = PR[1 + k];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            FL[v] = UL[v] * unL;
+            FR[v] = UR[v] * unR;
+        }
+        FL[1 + k] += PL[D + 1];
+        FR[1 + k] += PR[D + 1];
+        FL[D + 1] += PL[D + 1] * unL;
+        FR[D + 1] += PR[D + 1] * unR;
+        const double cL = sqrt(gam * PL[D + 1] / PL[0]);
+        const double cR = sqrt(gam * PR[D + 1] / PR[0]);
+        const double sL = fmin(unL - cL, unR - cR);
+        const double sR = fmax(unL + cL, unR + cR);
+        if (sL >= 0.0) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) F[v] = FL[v];
+        } else if (sR <= 0.0) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) F[v] = FR[v];
+        } else {
+            const double ids = 1.0 / (sR - sL);
+#pragma unroll
+            for (int v = 0; v < M; ++v) F[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) * ids;
+        }
+    }
+}
+
+template <int EQ, int M>
+__device__ __forceinline__ void source(const Grid& g, const double* q, double* S)
+{
+#pragma unroll
+    for (int v = 0; v < M; ++v) S[v] = 0.0;
+    if constexpr (EQ == 3) {
+        const double u = q[0];
+        S[0] = g.phys[1] * u * (1.0 - u) * (u - g.phys[2]);
+    }
+}
+
+template <int EQ, int D, int M>
+__device__ __forceinline__ double wave_speed(const Grid& g, const double* q)
+{
+    double s = 0.0;
+    if constexpr (EQ == 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += fabs(g.phys[k]);
+    } else if constexpr (EQ == 1) {
+        s = D * fabs(q[0]);
+    } else if constexpr (EQ == 2) {
+        const double gam = g.phys[0], rho = q[0];
+        double ke = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) ke += q[1 + k] * q[1 + k] / rho;
+        const double p = (gam - 1.0) * (q[D + 1] - 0.5 * ke);
+        const double c = sqrt(gam * p / rho);
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += fabs(q[1 + k] / rho) + c;
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------- host side
+struct Launch; // fwd
+
+// kernel launchers (defined in the .cu files), all on stream `st`
+void launch_stage(const Grid& g, cudaStream_t st, int u, int s, int lmin, double dtl, double bw,
+                  int reg);
+void launch_wave(const Grid& g, cudaStream_t st, int l);
+} // namespace mrlt

@@ -1,0 +1,29 @@
+// mrlt_tree.cuh -- host-side launcher of the tree kernels (private).
+#pragma once
+#include "mrlt_impl.cuh"
+
+namespace mrlt {
+
+enum ProjMode { PM_Q0 = 0, PM_Q1, PM_Q2, PM_REF2, PM_PRJ2, PM_REF3, PM_PRJ3, PM_MID };
+constexpr int MASS_BLOCKS = 64;
+
+struct Launcher {
+    Grid g;
+    cudaStream_t st = nullptr;
+    int* bc = nullptr; // compaction scratch, 2 ints per block of the largest level
+    long long n = 0;   // kernel launches issued
+
+    void project(int l, int mode);
+    void leaf_copy(int l, int from, int to);
+    void mark_refinements(int la);
+    void apply_tree(int la);
+    void compact(int l);
+    void reflux(int l);
+    void scale(int l);
+    void finite(int l);
+    void mass(int l, double* part);
+    void pack(int l, long long base, int* keys, double* vals);
+    void uniform(double* T, uint8_t* us);
+};
+
+} // namespace mrlt
