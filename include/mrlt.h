@@ -117,15 +117,28 @@ enum {
                                 end of each leaf's latest step                 */
     MR_READ_UNIFORM = 2,     /* double [m][2^{dL}]: the adapted solution rebuilt
                                 on the finest grid by the inverse MR transform  */
-    MR_READ_STATS = 3        /* double [64]: 0 t, 1 fine iterations, 2 macro steps,
+    MR_READ_STATS = 3,       /* double [64]: 0 t, 1 fine iterations, 2 macro steps,
                                 3 dt, 4 leaves, 5 nodes, 6 near-threshold details,
                                 7 leaf updates, 8..12 mass per variable,
                                 15 position in the macro step, 16+l leaves on level l */
+    MR_READ_PROFILE = 4      /* double [64]: 0 stage-kernel launches timed since
+                                mr_profile(h,1), 1 their summed device time (ms),
+                                2..4 leaf-stages they processed for stages 1..3,
+                                5 kernel launches of any kind in that window,
+                                16+l leaf-stages processed on level l (all time),
+                                40+l device time (ms) of the timed stage launches
+                                on level l */
 };
 
 /* Copy a result into the caller's host buffer.  With buf == NULL only *used
  * is set to the size needed; MR_E_INVALID if cap_bytes is too small. */
 mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap_bytes, size_t* used);
+
+/* Start (enable=1) or stop (enable=0) timing every stage-kernel launch with a
+ * pair of CUDA events on the solver's stream; enabling clears the previous
+ * totals.  Results are read with MR_READ_PROFILE.  Timing adds two event
+ * records per stage launch and nothing else. */
+mr_status mr_profile(mr_solver* h, int enable);
 
 /* Release everything owned by the handle (NULL is ignored). */
 void mr_destroy(mr_solver* h);

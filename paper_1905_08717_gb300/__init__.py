@@ -17,7 +17,7 @@ from . import inputs  # noqa: F401  (seeded synthetic initial data)
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "csrc", "libmrlt.so")
 
-MR_READ_LEAF_KEYS, MR_READ_LEAF_VALUES, MR_READ_UNIFORM, MR_READ_STATS = 0, 1, 2, 3
+MR_READ_LEAF_KEYS, MR_READ_LEAF_VALUES, MR_READ_UNIFORM, MR_READ_STATS, MR_READ_PROFILE = 0, 1, 2, 3, 4
 STATUS = {0: "MR_OK", 1: "MR_E_INVALID", 2: "MR_E_NOMEM", 3: "MR_E_CUDA",
           4: "MR_E_TIMEOUT", 5: "MR_E_STATE", 6: "MR_E_NUMERIC"}
 
@@ -62,6 +62,8 @@ def library() -> ctypes.CDLL:
         lib.mr_destroy.argtypes = [vp]
         lib.mr_last_error.argtypes = [vp]
         lib.mr_last_error.restype = ctypes.c_char_p
+        lib.mr_profile.argtypes = [vp, ctypes.c_int]
+        lib.mr_profile.restype = ctypes.c_int
         lib.mr_launch_count.argtypes = [vp]
         lib.mr_launch_count.restype = ll
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
@@ -174,6 +176,18 @@ class Solver:
                 "leaves": int(s[4]), "nodes": int(s[5]), "near": int(s[6]),
                 "updates": int(s[7]), "pos": int(s[15]), "mass": s[8:8 + self.m].copy(),
                 "leaves_per_level": s[16:17 + L].astype(np.int64)}
+
+    def profile(self, enable: bool):
+        """start / stop CUDA-event timing of the stage-kernel launches"""
+        self._check(library().mr_profile(self._h, int(enable)), "profile")
+
+    def profile_read(self) -> dict:
+        P = self._read(MR_READ_PROFILE, np.float64)
+        L = self.p.max_level
+        return {"stage_launches": int(P[0]), "stage_ms": float(P[1]),
+                "leaf_stages": P[2:5].astype(np.int64), "launches": int(P[5]),
+                "leaf_stages_per_level": P[16:17 + L].astype(np.int64),
+                "stage_ms_per_level": P[40:41 + L].copy()}
 
     def launch_count(self) -> int:
         return int(library().mr_launch_count(self._h))

@@ -27,6 +27,15 @@ struct mr_solver {
     long long iters = 0, macros = 0, pos = 0, stage_launches = 0;
     bool reg = false;
     std::string err;
+    // stage-kernel timing (mr_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;   // pairs: start 2i, stop 2i+1
+    int ev_used = 0;
+    std::vector<int> ev_level;     // level of each recorded pair
+    double prof_ms = 0.0;
+    double prof_level_ms[LMAX + 1] = {};
+    long long prof_launches = 0, prof_all0 = 0;
+    unsigned long long work0[(LMAX + 1) * 4] = {};
 };
 
 namespace {
@@ -92,6 +101,21 @@ int level_min(const mr_solver* h, long long n)
     return g.L;
 }
 
+// add the elapsed times of the recorded event pairs to the running total
+void drain_events(mr_solver* h)
+{
+    if (h->ev_used == 0) return;
+    cudaEventSynchronize(h->ev[2 * h->ev_used - 1]);
+    for (int i = 0; i < h->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) {
+            h->prof_ms += ms;
+            h->prof_level_ms[h->ev_level[i]] += ms;
+        }
+    }
+    h->ev_used = 0;
+}
+
 void stage(mr_solver* h, int u, int s, int lmin, double dtl)
 {
     const Grid& g = h->K.g;
@@ -99,7 +123,17 @@ void stage(mr_solver* h, int u, int s, int lmin, double dtl)
     static const double b3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
     const double b = g.rk == 2 ? b2[s - 1] : b3[s - 1];
     const int reg = h->reg && !g.gts;
-    launch_stage(g, h->stream, u, s, lmin, dtl, dtl * b, reg);
+    if (h->prof) {
+        if (h->ev_used * 2 + 2 > (int)h->ev.size()) drain_events(h);
+        cudaEventRecord(h->ev[2 * h->ev_used], h->stream);
+        h->ev_level[h->ev_used] = u;
+        launch_stage(g, h->stream, u, s, lmin, dtl, dtl * b, reg);
+        cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
+        ++h->ev_used;
+        ++h->prof_launches;
+    } else {
+        launch_stage(g, h->stream, u, s, lmin, dtl, dtl * b, reg);
+    }
     ++h->stage_launches;
 }
 
@@ -327,6 +361,9 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     A(dev_alloc(h, &g.near, 1));
     A(dev_alloc(h, &g.wmax, 1));
     A(dev_alloc(h, &g.updates, 1));
+    A(dev_alloc(h, &g.work, (LMAX + 1) * 4));
+    if (r == MR_OK && cudaMemset(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long)) != cudaSuccess)
+        r = MR_E_CUDA; // cumulative counters: never cleared by mr_reset
     A(dev_alloc(h, &h->K.bc, 2 * ((g.N[g.L] + NTHREADS - 1) / NTHREADS)));
     A(dev_alloc(h, &h->d_part, (size_t)(LMAX + 1) * MASS_BLOCKS * g.m));
     A(dev_alloc(h, &h->d_T, nd));
@@ -495,7 +532,7 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
     if (what == MR_READ_LEAF_KEYS) need = (size_t)nleaf * 4 * sizeof(int);
     else if (what == MR_READ_LEAF_VALUES) need = (size_t)nleaf * m * sizeof(double);
     else if (what == MR_READ_UNIFORM) need = (size_t)g.N[g.L] * m * sizeof(double);
-    else if (what == MR_READ_STATS) need = 64 * sizeof(double);
+    else if (what == MR_READ_STATS || what == MR_READ_PROFILE) need = 64 * sizeof(double);
     else return MR_E_INVALID;
     if (used) *used = need;
     if (!buf) return MR_OK;
@@ -509,6 +546,22 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
         }
         const void* src = what == MR_READ_LEAF_KEYS ? (const void*)h->d_keys : (const void*)h->d_T;
         if (need) MR_CK(cudaMemcpyAsync(buf, src, need, cudaMemcpyDeviceToHost, h->stream));
+    } else if (what == MR_READ_PROFILE) {
+        double* P = (double*)buf;
+        memset(P, 0, 64 * sizeof(double));
+        unsigned long long w[(LMAX + 1) * 4];
+        MR_CK(cudaMemcpyAsync(w, g.work, sizeof w, cudaMemcpyDeviceToHost, h->stream));
+        MR_CK(cudaStreamSynchronize(h->stream));
+        drain_events(h);
+        P[0] = (double)h->prof_launches;
+        P[1] = h->prof_ms;
+        for (int l = 0; l <= LMAX; ++l)
+            for (int s = 1; s <= 3; ++s) {
+                P[1 + s] += (double)(w[l * 4 + s] - h->work0[l * 4 + s]);
+                P[16 + l] += (double)w[l * 4 + s];
+            }
+        P[5] = (double)(h->K.n + h->stage_launches - h->prof_all0);
+        for (int l = 0; l <= LMAX; ++l) P[40 + l] = h->prof_level_ms[l];
     } else if (what == MR_READ_UNIFORM) {
         h->K.uniform(h->d_T, h->d_us);
         MR_CK(cudaMemcpyAsync(buf, h->d_T + g.off[g.L] * m, need, cudaMemcpyDeviceToHost, h->stream));
@@ -546,9 +599,34 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
     return sync_check(h);
 }
 
+mr_status mr_profile(mr_solver* h, int enable)
+{
+    if (!h) return MR_E_INVALID;
+    if (enable) {
+        if (h->ev.empty()) {
+            h->ev.resize(2 * 4096);
+            h->ev_level.assign(4096, 0);
+            for (auto& e : h->ev) MR_CK(cudaEventCreate(&e));
+        }
+        MR_CK(cudaStreamSynchronize(h->stream));
+        h->ev_used = 0;
+        h->prof_ms = 0.0;
+        for (double& x : h->prof_level_ms) x = 0.0;
+        h->prof_launches = 0;
+        h->prof_all0 = h->K.n + h->stage_launches;
+        MR_CK(cudaMemcpy(h->work0, h->K.g.work, sizeof h->work0, cudaMemcpyDeviceToHost));
+        h->prof = true;
+    } else {
+        drain_events(h);
+        h->prof = false;
+    }
+    return MR_OK;
+}
+
 void mr_destroy(mr_solver* h)
 {
     if (!h) return;
+    for (auto& e : h->ev) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     delete h;
 }

@@ -46,6 +46,7 @@ struct Grid {
     unsigned long long* near;
     unsigned long long* wmax;
     unsigned long long* updates;
+    unsigned long long* work;       // [(LMAX+1) * 4]: leaf-stages per level and stage
     long long off[LMAX + 1];
     long long N[LMAX + 1];
     int n[LMAX + 1];
@@ -244,11 +245,11 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
     }
     const int P0 = q[0] >> 1, P1 = q[1] >> 1, P2 = q[2] >> 1;
     const int a0 = q[0] & 1, a1 = q[1] & 1, a2 = q[2] & 1;
-#pragma unroll 1
+#pragma unroll
     for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
         const int z = D > 2 ? wrap_or_mirror(g, pl, 2, P2 + dz) : 0;
         const double wz = D > 2 ? pw(a2, dz) : 1.0;
-#pragma unroll 1
+#pragma unroll
         for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
             const int y = D > 1 ? wrap_or_mirror(g, pl, 1, P1 + dy) : 0;
             const double wyz = wz * (D > 1 ? pw(a1, dy) : 1.0);
@@ -291,41 +292,53 @@ __device__ __forceinline__ double minmod(double a, double b)
     return fabs(a) < fabs(b) ? a : b;
 }
 
-// numerical flux along direction k across the face between W[1] and W[2]
+// Variables that MUSCL reconstructs: primitives (rho, u_1..u_d, p) for Euler,
+// the conserved variable itself otherwise.
 template <int EQ, int D, int M>
-__device__ __forceinline__ void num_flux(const Grid& g, int k, double dxf, const double (&W)[4][M], double* F)
+__device__ __forceinline__ void recon_vars(const Grid& g, const double* W, double* P)
+{
+    if constexpr (EQ == 2) {
+        const double gam = g.phys[0];
+        const double rho = W[0];
+        const double ir = 1.0 / rho;
+        double ke = 0.0;
+        P[0] = rho;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            P[1 + c] = W[1 + c] * ir;
+            ke += W[1 + c] * P[1 + c];
+        }
+        P[D + 1] = (gam - 1.0) * (W[D + 1] - 0.5 * ke);
+    } else {
+#pragma unroll
+        for (int v = 0; v < M; ++v) P[v] = W[v];
+    }
+}
+
+// Numerical flux along direction k across the face between stencil cells 1
+// and 2 of a 4-cell stencil, from their reconstruction variables P(i, v).
+template <int EQ, int D, int M, class Acc>
+__device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, const Acc& P, double* F)
 {
     if constexpr (EQ == 0) { // linear advection, centred flux
-        F[0] = g.phys[k] * (W[1][0] + W[2][0]) * 0.5;
+        F[0] = g.phys[k] * (P(1, 0) + P(2, 0)) * 0.5;
     } else if constexpr (EQ == 3) { // two-point diffusive flux
-        F[0] = -g.phys[0] * (W[2][0] - W[1][0]) / dxf;
+        F[0] = -g.phys[0] * (P(2, 0) - P(1, 0)) / dxf;
     } else if constexpr (EQ == 1) { // Burgers: MUSCL-minmod + Godunov
-        const double uL = W[1][0] + 0.5 * minmod(W[1][0] - W[0][0], W[2][0] - W[1][0]);
-        const double uR = W[2][0] - 0.5 * minmod(W[2][0] - W[1][0], W[3][0] - W[2][0]);
+        const double u0 = P(0, 0), u1 = P(1, 0), u2 = P(2, 0), u3 = P(3, 0);
+        const double uL = u1 + 0.5 * minmod(u1 - u0, u2 - u1);
+        const double uR = u2 - 0.5 * minmod(u2 - u1, u3 - u2);
         const double fL = 0.5 * uL * uL, fR = 0.5 * uR * uR;
         if (uL <= uR) F[0] = uL > 0.0 ? fL : (uR < 0.0 ? fR : 0.0);
         else F[0] = fmax(fL, fR);
     } else { // Euler: MUSCL-minmod on (rho, u_1..u_d, p) + HLL
         const double gam = g.phys[0];
-        double P[4][M];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const double rho = W[i][0];
-            const double ir = 1.0 / rho;
-            double ke = 0.0;
-            P[i][0] = rho;
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                P[i][1 + c] = W[i][1 + c] * ir;
-                ke += W[i][1 + c] * P[i][1 + c];
-            }
-            P[i][D + 1] = (gam - 1.0) * (W[i][D + 1] - 0.5 * ke);
-        }
         double PL[M], PR[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-            PL[v] = P[1][v] + 0.5 * minmod(P[1][v] - P[0][v], P[2][v] - P[1][v]);
-            PR[v] = P[2][v] - 0.5 * minmod(P[2][v] - P[1][v], P[3][v] - P[2][v]);
+            const double a0 = P(0, v), a1 = P(1, v), a2 = P(2, v), a3 = P(3, v);
+            PL[v] = a1 + 0.5 * minmod(a1 - a0, a2 - a1);
+            PR[v] = a2 - 0.5 * minmod(a2 - a1, a3 - a2);
         }
         double UL[M], UR[M], FL[M], FR[M];
         double keL = 0.0, keR = 0.0;
@@ -367,6 +380,16 @@ __device__ __forceinline__ void num_flux(const Grid& g, int k, double dxf, const
             for (int v = 0; v < M; ++v) F[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) * ids;
         }
     }
+}
+
+// numerical flux from the conservative values of the 4 stencil cells
+template <int EQ, int D, int M>
+__device__ __forceinline__ void num_flux(const Grid& g, int k, double dxf, const double (&W)[4][M], double* F)
+{
+    double P[4][M];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) recon_vars<EQ, D, M>(g, W[i], P[i]);
+    flux_recon<EQ, D, M>(g, k, dxf, [&](int i, int v) { return P[i][v]; }, F);
 }
 
 template <int EQ, int M>

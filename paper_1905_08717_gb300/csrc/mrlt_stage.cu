@@ -1,6 +1,9 @@
-// mrlt_stage.cu -- the per-leaf stage kernel of the MR/MRLT time evolution:
-// face fluxes from the exposures of Secs. 4.1-4.3, the compact RK update of
-// Sec. 3 and the flux-register epilogue.  One thread per leaf of one level.
+// mrlt_stage.cu -- the stage kernels of the MR/MRLT time evolution: face
+// fluxes from the exposures of Secs. 4.1-4.3, the compact RK update of Sec. 3
+// and the flux-register epilogue.
+//  - k_stage_tile (d = 1, 2): one CTA per tile of one level; the halo is
+//    staged in shared memory and every face flux is computed once.
+//  - k_stage (d = 3): one thread per leaf.
 #include "mrlt_impl.cuh"
 
 namespace mrlt {
@@ -68,11 +71,45 @@ __device__ __forceinline__ int face_flux(const Grid& g, const Ctx& x, int u, con
     return kind;
 }
 
-// One compact RK stage (Sec. 3) of every leaf of level u:
-//   s = 1: q*  = q^n + dt_l f(q^n)
-//   s = 2: RK2 q^{n+1} = q^n/2 + q*/2 + dt_l f(q*)/2 ; RK3 q** = 3q^n/4 + q*/4 + dt_l f(q*)/4
-//   s = 3: q^{n+1} = q^n/3 + 2q**/3 + 2 dt_l f(q**)/3
-// f from the exposures of stage s; registers get dt_l * b_s * F at coarse-fine faces.
+// Compact RK update of one leaf from its right-hand side f (Sec. 3):
+//   s = 1: q*  = q^n + dt_l f
+//   s = 2: RK2 q^{n+1} = q^n/2 + q*/2 + dt_l f/2 ; RK3 q** = 3q^n/4 + q*/4 + dt_l f/4
+//   s = 3: q^{n+1} = q^n/3 + 2q**/3 + 2 dt_l f/3
+template <int M>
+__device__ __forceinline__ void rk_update(const Grid& g, int u, long long id, int s, double dtl, const double* f)
+{
+    const long long N = g.N[u];
+    double* q0 = fbase_w(g, F_Q0, u) + id;
+    double* q1 = fbase_w(g, F_Q1, u) + id;
+    double* q2 = fbase_w(g, F_Q2, u) + id;
+    double* qe = fbase_w(g, F_QE, u) + id;
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        const double kk = dtl * f[v];
+        if (s == 1) {
+            q1[v * N] = q0[v * N] + kk;
+        } else if (s == 2) {
+            if (g.rk == 2) qe[v * N] = 0.5 * q0[v * N] + 0.5 * q1[v * N] + 0.5 * kk;
+            else q2[v * N] = 0.75 * q0[v * N] + 0.25 * q1[v * N] + 0.25 * kk;
+        } else {
+            qe[v * N] = (1.0 / 3.0) * q0[v * N] + (2.0 / 3.0) * q2[v * N] + (2.0 / 3.0) * kk;
+        }
+    }
+}
+
+// flux registers (conservation across levels): dt_l b_s F at coarse-fine faces
+template <int M>
+__device__ __forceinline__ void reg_add(const Grid& g, int u, long long id, int fi, int kind, double bw,
+                                        const double* F)
+{
+    if (kind != K_FINER && kind != K_COARSER) return;
+    const long long N = g.N[u];
+    double* R = (kind == K_FINER ? g.rc : g.rf) + g.off[u] * g.nf * g.m + id;
+#pragma unroll
+    for (int v = 0; v < M; ++v) R[(fi * M + v) * N] += bw * F[v];
+}
+
+// One compact RK stage of every leaf of level u, one thread per leaf (d = 3).
 template <int EQ, int D>
 __global__ void __launch_bounds__(NTHREADS) k_stage(Grid g, int u, int s, int lmin, double dtl,
                                                     double bw, int reg)
@@ -81,8 +118,10 @@ __global__ void __launch_bounds__(NTHREADS) k_stage(Grid g, int u, int s, int lm
     const int cnt = g.counts[u];
     const int* list = g.leaves + g.off[u];
     const long long N = g.N[u];
-    if (s == 1 && blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(g.updates, (unsigned long long)cnt);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (s == 1) atomicAdd(g.updates, (unsigned long long)cnt);
+        atomicAdd(&g.work[u * 4 + s], (unsigned long long)cnt);
+    }
     const Ctx x{u, s, lmin};
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
         const long long id = list[t];
@@ -104,35 +143,223 @@ __global__ void __launch_bounds__(NTHREADS) k_stage(Grid g, int u, int s, int lm
 #pragma unroll
             for (int v = 0; v < M; ++v) f[v] += (Fm[v] - Fp[v]) * idx;
             if (reg) {
-                const long long roff = g.off[u] * g.nf * g.m;
-                if (km == K_FINER || km == K_COARSER) {
-                    double* R = (km == K_FINER ? g.rc : g.rf) + roff + id;
-#pragma unroll
-                    for (int v = 0; v < M; ++v) R[((2 * k) * M + v) * N] += bw * Fm[v];
-                }
-                if (kp == K_FINER || kp == K_COARSER) {
-                    double* R = (kp == K_FINER ? g.rc : g.rf) + roff + id;
-#pragma unroll
-                    for (int v = 0; v < M; ++v) R[((2 * k + 1) * M + v) * N] += bw * Fp[v];
-                }
+                reg_add<M>(g, u, id, 2 * k, km, bw, Fm);
+                reg_add<M>(g, u, id, 2 * k + 1, kp, bw, Fp);
             }
         }
-        double* q0 = fbase_w(g, F_Q0, u) + id;
-        double* q1 = fbase_w(g, F_Q1, u) + id;
-        double* q2 = fbase_w(g, F_Q2, u) + id;
-        double* qe = fbase_w(g, F_QE, u) + id;
+        rk_update<M>(g, u, id, s, dtl, f);
+    }
+}
+
+// Tile shapes of the tiled stage kernel: a CTA owns TX x TY cells of one level.
+template <int D> struct Tile;
+template <> struct Tile<1> { static constexpr int TX = 64, TY = 1; };
+template <> struct Tile<2> { static constexpr int TX = 16, TY = 16; };
+
+// Tiled stage (d = 1, 2).  The CTA
+//  1. reads the status of its tile and a 2-cell ring; leaves without work exit;
+//  2. stages in shared memory the exposure (Secs. 4.1-4.3) of every cell some
+//     leaf of the tile reads -- its radius-2 cross stencil, plus the 3^d block
+//     of a leaf facing an internal node -- and converts each cell once to the
+//     variables MUSCL reconstructs;
+//  3. computes every face touching a tile leaf once: on level u, or for a leaf
+//     against an internal node the mean of its 2^{d-1} sub-face fluxes on
+//     level u+1 (Sec. 2), the leaf's virtual children predicted (Eq. 4) from
+//     its shared 3^d block and the finer side read from level u+1;
+//  4. applies the compact RK update and the register epilogue to its leaves.
+template <int EQ, int D>
+__global__ void __launch_bounds__(Tile<D>::TX * Tile<D>::TY)
+k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
+{
+    constexpr int M = EQ == 2 ? D + 2 : 1;
+    constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, NT = TX * TY, H = 2;
+    constexpr int BX = TX + 2 * H, BY = D > 1 ? TY + 2 * H : 1, NB = BX * BY;
+    constexpr int NFX = (TX + 1) * TY, NFY = D > 1 ? TX * (TY + 1) : 1;
+    constexpr int OUT = 3; // status code of a cell past a wall
+    __shared__ double sW[M][NB];
+    __shared__ double sP[M][NB];
+    __shared__ double sFx[M][NFX];
+    __shared__ double sFy[M][NFY];
+    __shared__ uint8_t sSt[NB];
+
+    const int n = g.n[u];
+    const int ntx = (n + TX - 1) / TX;
+    const int ox = (blockIdx.x % ntx) * TX;
+    const int oy = D > 1 ? (blockIdx.x / ntx) * TY : 0;
+    const int tid = threadIdx.x;
+    const Ctx x{u, s, lmin};
+
+    // is block cell (bx, by) a leaf of this tile?
+    auto tile_leaf = [&](int bx, int by) -> bool {
+        if (bx < H || bx >= H + TX || ox + bx - H >= n) return false;
+        if (D > 1 && (by < H || by >= H + TY || oy + by - H >= n)) return false;
+        return sSt[by * BX + bx] == 1;
+    };
+    // a tile leaf with an internal node across one of its faces
+    auto leaf_li = [&](int bx, int by) -> bool {
+        if (u >= g.L || !tile_leaf(bx, by)) return false;
+        const int b = by * BX + bx;
+        bool li = sSt[b - 1] == 2 || sSt[b + 1] == 2;
+        if (D > 1) li = li || sSt[b - BX] == 2 || sSt[b + BX] == 2;
+        return li;
+    };
+
+    for (int b = tid; b < NB; b += NT) {
+        const int bx = b % BX, by = b / BX;
+        int qx, qy = 0;
+        const bool inb = in_box(g, u, 0, ox + bx - H, &qx) && (D < 2 || in_box(g, u, 1, oy + by - H, &qy));
+        sSt[b] = inb ? status(g, u, cell_id(g, u, qx, qy, 0)) : OUT;
+    }
+    __syncthreads();
+    const int nleaf = __syncthreads_count(tile_leaf(H + tid % TX, D > 1 ? H + tid / TX : 0));
+    if (nleaf == 0) return;
+    if (tid == 0) {
+        if (s == 1) atomicAdd(g.updates, (unsigned long long)nleaf);
+        atomicAdd(&g.work[u * 4 + s], (unsigned long long)nleaf);
+    }
+
+    // 2. exposures of the cells some tile leaf reads
+    for (int b = tid; b < NB; b += NT) {
+        const int bx = b % BX, by = b / BX;
+        bool need = false;
+#pragma unroll
+        for (int d = -2; d <= 2; ++d) {
+            need = need || tile_leaf(bx + d, by);
+            if (D > 1) need = need || tile_leaf(bx, by + d);
+        }
+#pragma unroll
+        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) need = need || leaf_li(bx + dx, by + dy);
+        if (!need) continue;
+        const int p[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, 0};
+        double W[M], P[M];
+        value_at<D, M>(g, x, u, p, W);
+        recon_vars<EQ, D, M>(g, W, P);
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-            const double kk = dtl * f[v];
-            if (s == 1) {
-                q1[v * N] = q0[v * N] + kk;
-            } else if (s == 2) {
-                if (g.rk == 2) qe[v * N] = 0.5 * q0[v * N] + 0.5 * q1[v * N] + 0.5 * kk;
-                else q2[v * N] = 0.75 * q0[v * N] + 0.25 * q1[v * N] + 0.25 * kk;
-            } else {
-                qe[v * N] = (1.0 / 3.0) * q0[v * N] + (2.0 / 3.0) * q2[v * N] + (2.0 / 3.0) * kk;
+            sW[v][b] = W[v];
+            sP[v][b] = P[v];
+        }
+    }
+    __syncthreads();
+
+    // 3. sub-face flux of the leaf at block index bl whose neighbour across
+    // (direction k, side) is an internal node
+    auto sub_flux = [&](int k, int side, int bl, double* F) {
+        const int bx = bl % BX, by = bl / BX;
+        const int c0 = ox + bx - H, c1 = D > 1 ? oy + by - H : 0;
+        constexpr int NTS = 1 << (D - 1);
+        double acc[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) acc[v] = 0.0;
+#pragma unroll 1
+        for (int t = 0; t < NTS; ++t) {
+            double P4[4][M];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                // stencil cell i on level u+1: fine coordinate along k, along the
+                // face, and whether it is a (virtual) child of the leaf
+                const int fk = (k == 0 ? 2 * c0 : 2 * c1) + (side > 0 ? i : i - 2);
+                const int ft = (k == 0 ? 2 * c1 : 2 * c0) + t;
+                const bool own = side > 0 ? i < 2 : i >= 2;
+                double W[M];
+                if (own) {
+                    const int ax = k == 0 ? (fk & 1) : (ft & 1);
+                    const int ay = k == 0 ? (ft & 1) : (fk & 1);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) W[v] = 0.0;
+#pragma unroll
+                    for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const double w = (D > 1 ? pw(ay, dy) : 1.0) * pw(ax, dx);
+                            const int bs = (by + dy) * BX + bx + dx;
+#pragma unroll
+                            for (int v = 0; v < M; ++v) W[v] += w * sW[v][bs];
+                        }
+                } else {
+                    int p[3] = {0, 0, 0};
+                    p[k] = fk;
+                    if (D > 1) p[1 - k] = ft;
+                    value_at<D, M>(g, x, u + 1, p, W);
+                }
+                recon_vars<EQ, D, M>(g, W, P4[i]);
+            }
+            double Fs[M];
+            flux_recon<EQ, D, M>(g, k, g.dx[u + 1][k], [&](int c, int v) { return P4[c][v]; }, Fs);
+#pragma unroll
+            for (int v = 0; v < M; ++v) acc[v] += Fs[v];
+        }
+#pragma unroll
+        for (int v = 0; v < M; ++v) F[v] = acc[v] * (1.0 / NTS);
+    };
+
+    // every face touching a tile leaf, each once
+    for (int f = tid; f < NFX; f += NT) {
+        const int i = f % (TX + 1), j = f / (TX + 1);
+        const int by = D > 1 ? H + j : 0;
+        const int bl = by * BX + H + i - 1, br = bl + 1;
+        const bool lL = tile_leaf(H + i - 1, by), lR = tile_leaf(H + i, by);
+        double F[M];
+        if (lL && sSt[br] == 2 && u < g.L) sub_flux(0, +1, bl, F);
+        else if (lR && sSt[bl] == 2 && u < g.L) sub_flux(0, -1, br, F);
+        else if (lL || lR)
+            flux_recon<EQ, D, M>(g, 0, g.dx[u][0], [&](int c, int v) { return sP[v][bl - 1 + c]; }, F);
+        else continue;
+#pragma unroll
+        for (int v = 0; v < M; ++v) sFx[v][f] = F[v];
+    }
+    if constexpr (D > 1) {
+        for (int f = tid; f < NFY; f += NT) {
+            const int i = f % TX, j = f / TX;
+            const int bb = (H + j - 1) * BX + H + i, bt = bb + BX;
+            const bool lB = tile_leaf(H + i, H + j - 1), lT = tile_leaf(H + i, H + j);
+            double F[M];
+            if (lB && sSt[bt] == 2 && u < g.L) sub_flux(1, +1, bb, F);
+            else if (lT && sSt[bb] == 2 && u < g.L) sub_flux(1, -1, bt, F);
+            else if (lB || lT)
+                flux_recon<EQ, D, M>(g, 1, g.dx[u][1], [&](int c, int v) { return sP[v][bb + (c - 1) * BX]; }, F);
+            else continue;
+#pragma unroll
+            for (int v = 0; v < M; ++v) sFy[v][f] = F[v];
+        }
+    }
+    __syncthreads();
+
+    // 4. compact RK update of the tile's leaves
+    {
+        const int i = tid % TX, j = D > 1 ? tid / TX : 0;
+        const int bx = H + i, by = D > 1 ? H + j : 0, b = by * BX + bx;
+        if (!tile_leaf(bx, by)) return;
+        const long long id = cell_id(g, u, ox + i, oy + j, 0);
+        double self[M], f[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) self[v] = sW[v][b];
+        source<EQ, M>(g, self, f);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int bm = k == 0 ? b - 1 : b - BX, bp = k == 0 ? b + 1 : b + BX;
+            const int fm = k == 0 ? j * (TX + 1) + i : j * TX + i;
+            const int fp = k == 0 ? fm + 1 : fm + TX;
+            const int sm = sSt[bm], sp = sSt[bp];
+            const int km = (sm == 2 && u < g.L) ? K_FINER : (sm == 1 ? K_LEAF : (sm == OUT ? K_WALL : K_COARSER));
+            const int kp = (sp == 2 && u < g.L) ? K_FINER : (sp == 1 ? K_LEAF : (sp == OUT ? K_WALL : K_COARSER));
+            double Fm[M], Fp[M];
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+                Fm[v] = k == 0 ? sFx[v][fm] : sFy[v][fm];
+                Fp[v] = k == 0 ? sFx[v][fp] : sFy[v][fp];
+            }
+            const double idx = 1.0 / g.dx[u][k];
+#pragma unroll
+            for (int v = 0; v < M; ++v) f[v] += (Fm[v] - Fp[v]) * idx;
+            if (reg) {
+                reg_add<M>(g, u, id, 2 * k, km, bw, Fm);
+                reg_add<M>(g, u, id, 2 * k + 1, kp, bw, Fp);
             }
         }
+        rk_update<M>(g, u, id, s, dtl, f);
     }
 }
 
@@ -171,7 +398,13 @@ template <int EQ, int D>
 static void stage_dispatch(const Grid& g, cudaStream_t st, int u, int s, int lmin, double dtl,
                            double bw, int reg)
 {
-    k_stage<EQ, D><<<grid_for(g, u), NTHREADS, 0, st>>>(g, u, s, lmin, dtl, bw, reg);
+    if constexpr (D <= 2) {
+        const long long ntx = (g.n[u] + Tile<D>::TX - 1) / Tile<D>::TX;
+        const long long tiles = D == 1 ? ntx : ntx * ((g.n[u] + Tile<D>::TY - 1) / Tile<D>::TY);
+        k_stage_tile<EQ, D><<<(unsigned)tiles, Tile<D>::TX * Tile<D>::TY, 0, st>>>(g, u, s, lmin, dtl, bw, reg);
+    } else {
+        k_stage<EQ, D><<<grid_for(g, u), NTHREADS, 0, st>>>(g, u, s, lmin, dtl, bw, reg);
+    }
 }
 
 void launch_stage(const Grid& g, cudaStream_t st, int u, int s, int lmin, double dtl, double bw, int reg)
@@ -187,10 +420,10 @@ void launch_stage(const Grid& g, cudaStream_t st, int u, int s, int lmin, double
 
 void launch_wave(const Grid& g, cudaStream_t st, int l)
 {
-#define MRLT_CASE(E, DD) \
-    if (g.eq == E && g.d == DD) {                                           \
-        k_wave<E, DD><<<grid_for(g, l), NTHREADS, 0, st>>>(g, l);           \
-        return;                                                             \
+#define MRLT_CASE(E, DD)                                          \
+    if (g.eq == E && g.d == DD) {                                 \
+        k_wave<E, DD><<<grid_for(g, l), NTHREADS, 0, st>>>(g, l); \
+        return;                                                   \
     }
     MRLT_CASE(0, 1) MRLT_CASE(0, 2) MRLT_CASE(0, 3)
     MRLT_CASE(1, 1) MRLT_CASE(1, 2) MRLT_CASE(1, 3)

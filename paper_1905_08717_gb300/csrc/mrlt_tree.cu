@@ -502,14 +502,18 @@ __global__ void k_scale(Grid g, int l)
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
     const long long N = g.N[l];
+    double mx[MMAX] = {0.0, 0.0, 0.0, 0.0, 0.0};
     GRID_STRIDE(t, cnt)
     {
         const long long id = list[t];
         if (id < 0 || id >= N) continue;
-        for (int v = 0; v < g.m; ++v) {
-            const double a = fabs(fbase(g, F_Q0, l)[v * N + id]);
+        for (int v = 0; v < g.m; ++v) mx[v] = fmax(mx[v], fabs(fbase(g, F_Q0, l)[v * N + id]));
+    }
+    for (int v = 0; v < g.m; ++v) {
+        double a = mx[v];
+        for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        if ((threadIdx.x & 31) == 0 && a > 0.0)
             atomicMax(&g.scale_bits[v], (unsigned long long)__double_as_longlong(a));
-        }
     }
 }
 
