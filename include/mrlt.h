@@ -140,6 +140,32 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap_bytes, size_t* u
  * records per stage launch and nothing else. */
 mr_status mr_profile(mr_solver* h, int enable);
 
+/* Total of every variable over a set of leaves, sum_i q_{i,v} |cell_i|, the
+ * same quantity as the mass entries of MR_READ_STATS, for callers that cannot
+ * allocate device memory: a process whose GPU memory is fully reserved by
+ * another allocator (a caching allocator, a fixed serving budget), or a
+ * latency-critical loop that must not pay for cudaMalloc and the device-wide
+ * synchronisation it implies.  The paper has no counterpart; it is a utility
+ * of this library.
+ *   keys_dev   device int32 [n_leaves][4] (level, i, j, k), as MR_READ_LEAF_KEYS
+ *   values_dev device float64 [n_leaves][m], as MR_READ_LEAF_VALUES
+ *   lo, hi     host double[dim]: the box, |cell| = prod_k (hi_k - lo_k) / 2^{d level}
+ *   mass_dev   device float64 [m], written
+ *   msg        optional host buffer (msg_cap bytes) for a readable error
+ * Limits: 1 <= m <= 5 variables, n_leaves <= INT_MAX; anything else returns
+ * MR_E_INVALID with the reason in msg.  The call allocates nothing: its only
+ * scratch is a fixed 10 KiB array in the library's device code, present on
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current), so make the first call on each device before any
+ * stream capture.  Work is only enqueued on cuda_stream: mass_dev is valid once
+ * the stream reaches it.  Every call uses the same array, which keeps the
+ * previous call's partial sums; calls that overlap on the GPU (other streams
+ * or other threads) race on it and must be serialised by the caller. */
+mr_status mr_leaf_mass_noalloc(int dim, const double* lo, const double* hi, const int* keys_dev,
+                               const double* values_dev, long long n_leaves, int m, double* mass_dev,
+                               void* cuda_stream, char* msg, size_t msg_cap);
+
 /* Release everything owned by the handle (NULL is ignored). */
 void mr_destroy(mr_solver* h);
 

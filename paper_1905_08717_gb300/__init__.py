@@ -66,8 +66,11 @@ def library() -> ctypes.CDLL:
         lib.mr_profile.restype = ctypes.c_int
         lib.mr_launch_count.argtypes = [vp]
         lib.mr_launch_count.restype = ll
+        lib.mr_leaf_mass_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), vp, vp, ll, ctypes.c_int,
+                                             vp, vp, ctypes.c_char_p, ctypes.c_size_t]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
-                     "mr_iterate", "mr_read"):
+                     "mr_iterate", "mr_read", "mr_leaf_mass_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -92,6 +95,22 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def leaf_mass_noalloc(dim: int, lo, hi, keys_ptr: int, values_ptr: int, n_leaves: int, m: int,
+                      mass_ptr: int, stream=None) -> None:
+    """Binding of mr_leaf_mass_noalloc: per-variable sum of q |cell| over leaves
+    whose keys / values already live in caller-owned device buffers (raw device
+    pointers), written to the caller's device buffer mass_ptr[m].  The call
+    allocates no device memory; the result is ready when `stream` reaches it."""
+    lib = library()
+    lo3 = (ctypes.c_double * 3)(*[float(x) for x in lo][:3])
+    hi3 = (ctypes.c_double * 3)(*[float(x) for x in hi][:3])
+    msg = ctypes.create_string_buffer(256)
+    r = lib.mr_leaf_mass_noalloc(dim, lo3, hi3, keys_ptr, values_ptr, n_leaves, m, mass_ptr,
+                                 ctypes.c_void_p(_stream_handle(stream)), msg, len(msg))
+    if r != 0:
+        raise MRError(r, msg.value.decode())
 
 
 def _dptr(a: np.ndarray):

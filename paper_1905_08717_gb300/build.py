@@ -1,6 +1,6 @@
 """Build the CUDA library libmrlt.so in-tree for sm_103a (GB300) with nvcc.
 
-The three translation units are compiled in parallel and linked with the
+The translation units are compiled in parallel and linked with the
 static CUDA runtime.  Run as `python -m paper_1905_08717_gb300.build`.
 """
 from __future__ import annotations
@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "libmrlt.so")
-SOURCES = ["mrlt_api.cu", "mrlt_tree.cu", "mrlt_stage.cu"]
+SOURCES = ["mrlt_api.cu", "mrlt_tree.cu", "mrlt_stage.cu", "mrlt_noalloc.cu"]
 HEADERS = ["mrlt_impl.cuh", "mrlt_tree.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
