@@ -336,7 +336,10 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
         g.off[l] = off;
         g.N[l] = 1LL << (g.d * l);
         g.n[l] = 1 << l;
-        for (int k = 0; k < 3; ++k) g.dx[l][k] = (cfg->hi[k] - cfg->lo[k]) / g.n[l];
+        for (int k = 0; k < 3; ++k) {
+            g.dx[l][k] = (cfg->hi[k] - cfg->lo[k]) / g.n[l];
+            g.rdx[l][k] = 1.0 / g.dx[l][k];
+        }
         off += g.N[l];
     }
     h->ntot = off;

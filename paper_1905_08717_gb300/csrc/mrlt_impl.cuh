@@ -51,6 +51,7 @@ struct Grid {
     long long N[LMAX + 1];
     int n[LMAX + 1];
     double dx[LMAX + 1][3];
+    double rdx[LMAX + 1][3];        // 1 / dx
     int d, m, nf, L, lb, eq, rk, gts;
     int bc[3];
     double phys[8];

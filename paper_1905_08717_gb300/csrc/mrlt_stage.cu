@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NTHREADS) k_stage(Grid g, int u, int s, int lm
             double Fm[M], Fp[M];
             const int km = face_flux<EQ, D, M>(g, x, u, c, k, -1, Fm);
             const int kp = face_flux<EQ, D, M>(g, x, u, c, k, +1, Fp);
-            const double idx = 1.0 / g.dx[u][k];
+            const double idx = g.rdx[u][k];
 #pragma unroll
             for (int v = 0; v < M; ++v) f[v] += (Fm[v] - Fp[v]) * idx;
             if (reg) {
@@ -156,17 +156,41 @@ template <int D> struct Tile;
 template <> struct Tile<1> { static constexpr int TX = 64, TY = 1; };
 template <> struct Tile<2> { static constexpr int TX = 16, TY = 16; };
 
+// Append, in thread order, the items for which `take` holds to a shared list
+// (warp ballots and a block-wide prefix); every thread of the block calls it
+// with the same `len` and gets the new length.
+template <int NT>
+__device__ __forceinline__ int block_append(bool take, int item, short* list, int len, int* sWarp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) sWarp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        const int c = sWarp[w];
+        before += w < warp ? c : 0;
+        total += c;
+    }
+    if (take) list[len + before + __popc(bal & ((1u << lane) - 1u))] = (short)item;
+    __syncthreads();
+    return len + total;
+}
+
 // Tiled stage (d = 1, 2).  The CTA
-//  1. reads the status of its tile and a 2-cell ring; leaves without work exit;
-//  2. stages in shared memory the exposure (Secs. 4.1-4.3) of every cell some
-//     leaf of the tile reads -- its radius-2 cross stencil, plus the 3^d block
-//     of a leaf facing an internal node -- and converts each cell once to the
-//     variables MUSCL reconstructs;
-//  3. computes every face touching a tile leaf once: on level u, or for a leaf
-//     against an internal node the mean of its 2^{d-1} sub-face fluxes on
-//     level u+1 (Sec. 2), the leaf's virtual children predicted (Eq. 4) from
-//     its shared 3^d block and the finer side read from level u+1;
+//  1. reads the status of its tile and a 2-cell ring; tiles without leaves exit;
+//  2. lists the cells some leaf of the tile reads -- its radius-2 cross stencil,
+//     plus the 3^d block of a leaf facing an internal node -- and stages their
+//     exposures (Secs. 4.1-4.3) and reconstruction variables in shared memory,
+//     stored nodes first, then virtual cells and ghosts;
+//  3. lists the faces touching a tile leaf and computes each once: plain faces
+//     on level u from the shared cells; faces of a leaf against an internal node
+//     as the mean of 2^{d-1} sub-face fluxes on level u+1 (Sec. 2), one thread
+//     per sub-face, the leaf's virtual children predicted (Eq. 4) from its
+//     shared 3^d block and the finer side read from level u+1;
 //  4. applies the compact RK update and the register epilogue to its leaves.
+// Work lists keep every warp on one kind of work.
 template <int EQ, int D>
 __global__ void __launch_bounds__(Tile<D>::TX * Tile<D>::TY)
 k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
@@ -174,13 +198,16 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
     constexpr int M = EQ == 2 ? D + 2 : 1;
     constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, NT = TX * TY, H = 2;
     constexpr int BX = TX + 2 * H, BY = D > 1 ? TY + 2 * H : 1, NB = BX * BY;
-    constexpr int NFX = (TX + 1) * TY, NFY = D > 1 ? TX * (TY + 1) : 1;
-    constexpr int OUT = 3; // status code of a cell past a wall
+    constexpr int NFX = (TX + 1) * TY, NFY = D > 1 ? TX * (TY + 1) : 0, NF = NFX + NFY;
+    constexpr int NTS = 1 << (D - 1); // sub-faces per face
+    constexpr int NL = NB > NF ? NB : NF;
+    constexpr int OUT = 3;            // status code of a cell past a wall
     __shared__ double sW[M][NB];
     __shared__ double sP[M][NB];
-    __shared__ double sFx[M][NFX];
-    __shared__ double sFy[M][NFY];
+    __shared__ double sF[M][NF];      // x faces [0, NFX), y faces [NFX, NF)
     __shared__ uint8_t sSt[NB];
+    __shared__ short sList[NL];
+    __shared__ int sWarp[NT / 32];
 
     const int n = g.n[u];
     const int ntx = (n + TX - 1) / TX;
@@ -188,6 +215,7 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
     const int oy = D > 1 ? (blockIdx.x / ntx) * TY : 0;
     const int tid = threadIdx.x;
     const Ctx x{u, s, lmin};
+    const bool finer = u < g.L; // internal nodes of level u have children
 
     // is block cell (bx, by) a leaf of this tile?
     auto tile_leaf = [&](int bx, int by) -> bool {
@@ -197,13 +225,47 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
     };
     // a tile leaf with an internal node across one of its faces
     auto leaf_li = [&](int bx, int by) -> bool {
-        if (u >= g.L || !tile_leaf(bx, by)) return false;
+        if (!finer || !tile_leaf(bx, by)) return false;
         const int b = by * BX + bx;
         bool li = sSt[b - 1] == 2 || sSt[b + 1] == 2;
         if (D > 1) li = li || sSt[b - BX] == 2 || sSt[b + BX] == 2;
         return li;
     };
+    auto needed = [&](int b) -> bool {
+        const int bx = b % BX, by = b / BX;
+        bool need = false;
+#pragma unroll
+        for (int d = -2; d <= 2; ++d) {
+            need = need || tile_leaf(bx + d, by);
+            if (D > 1) need = need || tile_leaf(bx, by + d);
+        }
+#pragma unroll
+        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) need = need || leaf_li(bx + dx, by + dy);
+        return need;
+    };
+    // geometry of face f: the cells on its two sides and the direction
+    auto face = [&](int f, int& k, int& lo, int& hi, bool& leafLo, bool& leafHi) {
+        if (f < NFX) {
+            const int i = f % (TX + 1), j = f / (TX + 1);
+            const int by = D > 1 ? H + j : 0;
+            k = 0;
+            lo = by * BX + H + i - 1;
+            hi = lo + 1;
+            leafLo = tile_leaf(H + i - 1, by);
+            leafHi = tile_leaf(H + i, by);
+        } else {
+            const int ff = f - NFX, i = ff % TX, j = ff / TX;
+            k = 1;
+            lo = (H + j - 1) * BX + H + i;
+            hi = lo + BX;
+            leafLo = tile_leaf(H + i, H + j - 1);
+            leafHi = tile_leaf(H + i, H + j);
+        }
+    };
 
+    // 1. status of the tile and its ring
     for (int b = tid; b < NB; b += NT) {
         const int bx = b % BX, by = b / BX;
         int qx, qy = 0;
@@ -218,23 +280,30 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
         atomicAdd(&g.work[u * 4 + s], (unsigned long long)nleaf);
     }
 
-    // 2. exposures of the cells some tile leaf reads
-    for (int b = tid; b < NB; b += NT) {
+    // 2. exposures of the needed cells: stored nodes, then the others
+    int nst = 0;
+    for (int b0 = 0; b0 < NB; b0 += NT) {
+        const int b = b0 + tid;
+        nst = block_append<NT>(b < NB && (sSt[b] == 1 || sSt[b] == 2) && needed(b), b, sList, nst, sWarp);
+    }
+    int ncell = nst;
+    for (int b0 = 0; b0 < NB; b0 += NT) {
+        const int b = b0 + tid;
+        ncell = block_append<NT>(b < NB && sSt[b] != 1 && sSt[b] != 2 && needed(b), b, sList, ncell, sWarp);
+    }
+    for (int t = tid; t < ncell; t += NT) {
+        const int b = sList[t];
         const int bx = b % BX, by = b / BX;
-        bool need = false;
-#pragma unroll
-        for (int d = -2; d <= 2; ++d) {
-            need = need || tile_leaf(bx + d, by);
-            if (D > 1) need = need || tile_leaf(bx, by + d);
-        }
-#pragma unroll
-        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) need = need || leaf_li(bx + dx, by + dy);
-        if (!need) continue;
-        const int p[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, 0};
         double W[M], P[M];
-        value_at<D, M>(g, x, u, p, W);
+        if (t < nst) {
+            int qx, qy = 0;
+            in_box(g, u, 0, ox + bx - H, &qx);
+            if (D > 1) in_box(g, u, 1, oy + by - H, &qy);
+            expose<M>(g, x, u, cell_id(g, u, qx, qy, 0), sSt[b], W);
+        } else {
+            const int p[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, 0};
+            value_at<D, M>(g, x, u, p, W);
+        }
         recon_vars<EQ, D, M>(g, W, P);
 #pragma unroll
         for (int v = 0; v < M; ++v) {
@@ -244,22 +313,68 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
     }
     __syncthreads();
 
-    // 3. sub-face flux of the leaf at block index bl whose neighbour across
-    // (direction k, side) is an internal node
-    auto sub_flux = [&](int k, int side, int bl, double* F) {
-        const int bx = bl % BX, by = bl / BX;
-        const int c0 = ox + bx - H, c1 = D > 1 ? oy + by - H : 0;
-        constexpr int NTS = 1 << (D - 1);
-        double acc[M];
+    // 3a. plain faces on level u
+    int nfl = 0;
+    for (int f0 = 0; f0 < NF; f0 += NT) {
+        const int f = f0 + tid;
+        bool take = false;
+        if (f < NF) {
+            int k, lo, hi;
+            bool lL, lH;
+            face(f, k, lo, hi, lL, lH);
+            const bool sub = finer && ((lL && sSt[hi] == 2) || (lH && sSt[lo] == 2));
+            take = (lL || lH) && !sub;
+        }
+        nfl = block_append<NT>(take, f, sList, nfl, sWarp);
+    }
+    for (int t = tid; t < nfl; t += NT) {
+        const int f = sList[t];
+        int k, lo, hi;
+        bool lL, lH;
+        face(f, k, lo, hi, lL, lH);
+        const int stride = k == 0 ? 1 : BX;
+        double F[M];
+        flux_recon<EQ, D, M>(g, k, g.dx[u][k], [&](int c, int v) { return sP[v][lo + (c - 1) * stride]; }, F);
 #pragma unroll
-        for (int v = 0; v < M; ++v) acc[v] = 0.0;
-#pragma unroll 1
-        for (int t = 0; t < NTS; ++t) {
+        for (int v = 0; v < M; ++v) sF[v][f] = F[v];
+    }
+    __syncthreads();
+
+    // 3b. faces of a leaf against an internal node: one thread per sub-face
+    int nsb = 0;
+    if (finer) {
+        for (int f0 = 0; f0 < NF; f0 += NT) {
+            const int f = f0 + tid;
+            bool take = false;
+            if (f < NF) {
+                int k, lo, hi;
+                bool lL, lH;
+                face(f, k, lo, hi, lL, lH);
+                take = (lL && sSt[hi] == 2) || (lH && sSt[lo] == 2);
+            }
+            nsb = block_append<NT>(take, f, sList, nsb, sWarp);
+        }
+    }
+    for (int base = 0; base < nsb * NTS; base += NT) {
+        const int task = base + tid;
+        const bool act = task < nsb * NTS;
+        const int f = act ? sList[task / NTS] : 0, t = task % NTS;
+        double F[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) F[v] = 0.0;
+        if (act) {
+            int k, lo, hi;
+            bool lL, lH;
+            face(f, k, lo, hi, lL, lH);
+            const bool leafIsLo = lL && sSt[hi] == 2;
+            const int bl = leafIsLo ? lo : hi, side = leafIsLo ? 1 : -1;
+            const int bx = bl % BX, by = bl / BX;
+            const int c0 = ox + bx - H, c1 = D > 1 ? oy + by - H : 0;
             double P4[4][M];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                // stencil cell i on level u+1: fine coordinate along k, along the
-                // face, and whether it is a (virtual) child of the leaf
+                // stencil cell i on level u+1: fine coordinate along k and along
+                // the face; the leaf's own children are virtual
                 const int fk = (k == 0 ? 2 * c0 : 2 * c1) + (side > 0 ? i : i - 2);
                 const int ft = (k == 0 ? 2 * c1 : 2 * c0) + t;
                 const bool own = side > 0 ? i < 2 : i >= 2;
@@ -286,43 +401,17 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
                 }
                 recon_vars<EQ, D, M>(g, W, P4[i]);
             }
-            double Fs[M];
-            flux_recon<EQ, D, M>(g, k, g.dx[u + 1][k], [&](int c, int v) { return P4[c][v]; }, Fs);
-#pragma unroll
-            for (int v = 0; v < M; ++v) acc[v] += Fs[v];
+            flux_recon<EQ, D, M>(g, k, g.dx[u + 1][k], [&](int c, int v) { return P4[c][v]; }, F);
         }
+        if constexpr (NTS == 2) { // the two sub-faces of a face sit in lanes 2i, 2i+1
 #pragma unroll
-        for (int v = 0; v < M; ++v) F[v] = acc[v] * (1.0 / NTS);
-    };
-
-    // every face touching a tile leaf, each once
-    for (int f = tid; f < NFX; f += NT) {
-        const int i = f % (TX + 1), j = f / (TX + 1);
-        const int by = D > 1 ? H + j : 0;
-        const int bl = by * BX + H + i - 1, br = bl + 1;
-        const bool lL = tile_leaf(H + i - 1, by), lR = tile_leaf(H + i, by);
-        double F[M];
-        if (lL && sSt[br] == 2 && u < g.L) sub_flux(0, +1, bl, F);
-        else if (lR && sSt[bl] == 2 && u < g.L) sub_flux(0, -1, br, F);
-        else if (lL || lR)
-            flux_recon<EQ, D, M>(g, 0, g.dx[u][0], [&](int c, int v) { return sP[v][bl - 1 + c]; }, F);
-        else continue;
+            for (int v = 0; v < M; ++v) {
+                const double other = __shfl_xor_sync(0xffffffffu, F[v], 1);
+                if (act && t == 0) sF[v][f] = (F[v] + other) * 0.5;
+            }
+        } else if (act) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) sFx[v][f] = F[v];
-    }
-    if constexpr (D > 1) {
-        for (int f = tid; f < NFY; f += NT) {
-            const int i = f % TX, j = f / TX;
-            const int bb = (H + j - 1) * BX + H + i, bt = bb + BX;
-            const bool lB = tile_leaf(H + i, H + j - 1), lT = tile_leaf(H + i, H + j);
-            double F[M];
-            if (lB && sSt[bt] == 2 && u < g.L) sub_flux(1, +1, bb, F);
-            else if (lT && sSt[bb] == 2 && u < g.L) sub_flux(1, -1, bt, F);
-            else if (lB || lT)
-                flux_recon<EQ, D, M>(g, 1, g.dx[u][1], [&](int c, int v) { return sP[v][bb + (c - 1) * BX]; }, F);
-            else continue;
-#pragma unroll
-            for (int v = 0; v < M; ++v) sFy[v][f] = F[v];
+            for (int v = 0; v < M; ++v) sF[v][f] = F[v];
         }
     }
     __syncthreads();
@@ -340,18 +429,18 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             const int bm = k == 0 ? b - 1 : b - BX, bp = k == 0 ? b + 1 : b + BX;
-            const int fm = k == 0 ? j * (TX + 1) + i : j * TX + i;
+            const int fm = k == 0 ? j * (TX + 1) + i : NFX + j * TX + i;
             const int fp = k == 0 ? fm + 1 : fm + TX;
             const int sm = sSt[bm], sp = sSt[bp];
-            const int km = (sm == 2 && u < g.L) ? K_FINER : (sm == 1 ? K_LEAF : (sm == OUT ? K_WALL : K_COARSER));
-            const int kp = (sp == 2 && u < g.L) ? K_FINER : (sp == 1 ? K_LEAF : (sp == OUT ? K_WALL : K_COARSER));
+            const int km = (sm == 2 && finer) ? K_FINER : (sm == 1 ? K_LEAF : (sm == OUT ? K_WALL : K_COARSER));
+            const int kp = (sp == 2 && finer) ? K_FINER : (sp == 1 ? K_LEAF : (sp == OUT ? K_WALL : K_COARSER));
             double Fm[M], Fp[M];
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                Fm[v] = k == 0 ? sFx[v][fm] : sFy[v][fm];
-                Fp[v] = k == 0 ? sFx[v][fp] : sFy[v][fp];
+                Fm[v] = sF[v][fm];
+                Fp[v] = sF[v][fp];
             }
-            const double idx = 1.0 / g.dx[u][k];
+            const double idx = g.rdx[u][k];
 #pragma unroll
             for (int v = 0; v < M; ++v) f[v] += (Fm[v] - Fp[v]) * idx;
             if (reg) {
