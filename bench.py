@@ -48,7 +48,10 @@ def _args():
     ap.add_argument("--t-end", type=float, default=T_END)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-run", action="store_true",
-                    help="only the timed LT solves (no e2e / GTS / peaks); for ncu launch lists")
+                    help="only the timed LT solves (no e2e / GTS / peaks); for ncu captures")
+    ap.add_argument("--level", type=int, default=10, help="finest level (profiling runs)")
+    ap.add_argument("--eps", type=float, default=1e-3, help="threshold (profiling runs)")
+    ap.add_argument("--min-level", type=int, default=3, help="coarsest leaf level (profiling runs)")
     return ap.parse_args()
 
 
@@ -203,7 +206,10 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
-    p, q = inputs.euler_2d_quadrants(L=10, eps=1e-3, seed=0)
+    if args.profile_run:
+        p, q = inputs.euler_2d_quadrants(L=args.level, eps=args.eps, seed=0, min_level=args.min_level)
+    else:
+        p, q = inputs.euler_2d_quadrants(L=10, eps=1e-3, seed=0)
     q_pin = torch.from_numpy(q).pin_memory()
     qn = q_pin.numpy()
     n = 1 << p.max_level
@@ -248,9 +254,13 @@ def run_ours(args):
     st = solver.stats()
     if args.profile_run:
         if rank == 0:
+            ls = prof["leaf_stages_per_level"]
             print(json.dumps({"profile_run": True, "ms_per_step": 1e3 * total_s / args.steps,
                               "updates": updates, "stage_ms": prof["stage_ms"],
-                              "stage_launches": prof["stage_launches"], "launches": launches}))
+                              "stage_launches": prof["stage_launches"], "launches": launches,
+                              "level": args.level, "eps": args.eps, "min_level": args.min_level,
+                              "leaf_stages_per_level": [int(x) for x in ls],
+                              "stage_ms_per_level": [round(float(x), 3) for x in prof["stage_ms_per_level"]]}))
         return
 
     # ---- end to end through the C-ABI with host buffers: H2D of q0 from pinned

@@ -116,25 +116,28 @@ void drain_events(mr_solver* h)
     h->ev_used = 0;
 }
 
-void stage(mr_solver* h, int u, int s, int lmin, double dtl)
+// one compact RK stage s on the leaves of levels lo..hi (one launch when the
+// levels are independent); dt is the finest-level step
+void stage(mr_solver* h, int lo, int hi, int s, int lmin, double dt)
 {
     const Grid& g = h->K.g;
     static const double b2[2] = {0.5, 0.5};
     static const double b3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
     const double b = g.rk == 2 ? b2[s - 1] : b3[s - 1];
     const int reg = h->reg && !g.gts;
+    int launched;
     if (h->prof) {
         if (h->ev_used * 2 + 2 > (int)h->ev.size()) drain_events(h);
         cudaEventRecord(h->ev[2 * h->ev_used], h->stream);
-        h->ev_level[h->ev_used] = u;
-        launch_stage(g, h->stream, u, s, lmin, dtl, dtl * b, reg);
+        h->ev_level[h->ev_used] = hi;
+        launched = launch_stage(g, h->stream, lo, hi, s, lmin, dt, b, reg);
         cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
         ++h->ev_used;
-        ++h->prof_launches;
+        h->prof_launches += launched;
     } else {
-        launch_stage(g, h->stream, u, s, lmin, dtl, dtl * b, reg);
+        launched = launch_stage(g, h->stream, lo, hi, s, lmin, dt, b, reg);
     }
-    ++h->stage_launches;
+    h->stage_launches += launched;
 }
 
 mr_status sync_check(mr_solver* h)
@@ -178,27 +181,27 @@ mr_status lt_iteration(mr_solver* h, long long n, long long nit)
     Grid& g = h->K.g;
     const int L = g.L, lb = g.lb, lmin = level_min(h, n);
     const double dt = h->dt;
-    for (int l = lmin; l <= L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    h->K.leaf_copy(lmin, L, F_QE, F_Q0);
     for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_Q0);
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
         MR_TRY(adapt(h, lmin));
     if (lmin > lb) h->K.project(lmin - 1, PM_MID);
-    for (int l = L; l >= lmin; --l) stage(h, l, 1, lmin, ldexp(dt, L - l));
+    stage(h, lmin, L, 1, lmin, dt); // first stage: all active levels at once
     for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF2);
     for (int l = L; l >= lmin; --l) {
         if (l < L) h->K.project(l, PM_PRJ2);
-        stage(h, l, 2, lmin, ldexp(dt, L - l));
+        stage(h, l, l, 2, lmin, dt);
     }
     if (g.rk == 3) {
         for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF3);
         for (int l = L; l >= lmin; --l) {
             if (l < L) h->K.project(l, PM_PRJ3);
-            stage(h, l, 3, lmin, ldexp(dt, L - l));
+            stage(h, l, l, 3, lmin, dt);
         }
     }
     if (h->reg) {
         const int lc = (n + 1 == nit) ? lb : level_min(h, n + 1);
-        for (int l = lc; l < L; ++l) h->K.reflux(l);
+        if (lc < L) h->K.reflux(lc, L - 1);
     }
     return MR_OK;
 }
@@ -208,16 +211,16 @@ mr_status gts_iteration(mr_solver* h, long long n)
 {
     Grid& g = h->K.g;
     const int L = g.L, lb = g.lb;
-    for (int l = lb; l <= L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    h->K.leaf_copy(lb, L, F_QE, F_Q0);
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
         MR_TRY(adapt(h, lb));
-    for (int l = L; l >= lb; --l) stage(h, l, 1, lb, h->dt);
+    stage(h, lb, L, 1, lb, h->dt); // every level at the same instant: one launch per stage
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q1);
-    for (int l = L; l >= lb; --l) stage(h, l, 2, lb, h->dt);
+    stage(h, lb, L, 2, lb, h->dt);
     if (g.rk == 3) {
         for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q2);
-        for (int l = L; l >= lb; --l) stage(h, l, 3, lb, h->dt);
+        stage(h, lb, L, 3, lb, h->dt);
     }
     return MR_OK;
 }
@@ -286,7 +289,7 @@ mr_status init_state(mr_solver* h, const double* q0)
         MR_CK(cudaMemsetAsync(g.rf, 0, nd * g.nf * sizeof(double), h->stream));
     }
     MR_CK(cudaMemsetAsync(g.flag, 0, h->ntot, h->stream));
-    MR_CK(cudaMemsetAsync(g.counts, 0, 2 * (LMAX + 1) * sizeof(int), h->stream));
+    MR_CK(cudaMemsetAsync(g.counts, 0, 3 * (LMAX + 1) * sizeof(int), h->stream));
     MR_CK(cudaMemsetAsync(g.err, 0, sizeof(int), h->stream));
     MR_CK(cudaMemsetAsync(g.near, 0, sizeof(unsigned long long), h->stream));
     MR_CK(cudaMemsetAsync(g.updates, 0, sizeof(unsigned long long), h->stream));
@@ -297,7 +300,7 @@ mr_status init_state(mr_solver* h, const double* q0)
     for (int l = g.lb; l <= g.L; ++l) h->K.compact(l);
     for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
     if (h->cfg.adapt_mode != MR_ADAPT_NEVER) MR_TRY(adapt(h, g.lb));
-    for (int l = g.lb; l <= g.L; ++l) h->K.leaf_copy(l, F_Q0, F_QE);
+    h->K.leaf_copy(g.lb, g.L, F_Q0, F_QE);
     h->t = h->dt = 0.0;
     h->iters = h->macros = h->pos = 0;
     return sync_check(h);
@@ -331,8 +334,12 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     for (int k = 0; k < 8; ++k) g.phys[k] = cfg->phys[k];
     g.eps = cfg->eps;
     g.eps_mode = cfg->eps_mode;
-    long long off = 0;
+    long long off = 0, toff = 0;
     for (int l = g.lb; l <= g.L; ++l) {
+        g.toff[l] = toff;
+        g.ntx[l] = g.d == 1 ? (int)((1LL << l) + kTile1X - 1) / kTile1X : (int)((1LL << l) + kTile2X - 1) / kTile2X;
+        g.nty[l] = g.d == 2 ? (int)((1LL << l) + kTile2Y - 1) / kTile2Y : 1;
+        toff += (long long)g.ntx[l] * g.nty[l];
         g.off[l] = off;
         g.N[l] = 1LL << (g.d * l);
         g.n[l] = 1 << l;
@@ -358,7 +365,9 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     }
     A(dev_alloc(h, &g.leaves, off));
     A(dev_alloc(h, &g.inner, off));
-    A(dev_alloc(h, &g.counts, 2 * (LMAX + 1)));
+    A(dev_alloc(h, &g.counts, 3 * (LMAX + 1)));
+    A(dev_alloc(h, &g.tflag, (size_t)toff));
+    A(dev_alloc(h, &g.tlist, (size_t)toff));
     A(dev_alloc(h, &g.scale_bits, MMAX));
     A(dev_alloc(h, &g.err, 1));
     A(dev_alloc(h, &g.near, 1));
@@ -458,7 +467,7 @@ mr_status mr_set_tree(mr_solver* h, const unsigned char* lev)
                         }
                     }
         }
-    for (int l = lb; l <= L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    h->K.leaf_copy(lb, L, F_QE, F_Q0);
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
     MR_CK(cudaMemsetAsync(g.flag, 0, h->ntot, h->stream));
     std::vector<uint8_t> fl((size_t)h->ntot, 0);
@@ -469,7 +478,7 @@ mr_status mr_set_tree(mr_solver* h, const unsigned char* lev)
     h->K.apply_tree(lb);
     for (int l = lb; l <= L; ++l) h->K.compact(l);
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
-    for (int l = lb; l <= L; ++l) h->K.leaf_copy(l, F_Q0, F_QE);
+    h->K.leaf_copy(lb, L, F_Q0, F_QE);
     return sync_check(h);
 }
 
@@ -478,10 +487,10 @@ mr_status mr_adapt(mr_solver* h)
     if (!h) return MR_E_INVALID;
     if (h->pos != 0) return MR_E_STATE;
     Grid& g = h->K.g;
-    for (int l = g.lb; l <= g.L; ++l) h->K.leaf_copy(l, F_QE, F_Q0);
+    h->K.leaf_copy(g.lb, g.L, F_QE, F_Q0);
     for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
     MR_TRY(adapt(h, g.lb));
-    for (int l = g.lb; l <= g.L; ++l) h->K.leaf_copy(l, F_Q0, F_QE);
+    h->K.leaf_copy(g.lb, g.L, F_Q0, F_QE);
     return sync_check(h);
 }
 

@@ -25,6 +25,9 @@ namespace mrlt {
 constexpr int LMAX = 16;
 constexpr int MMAX = 5;
 constexpr int NTHREADS = 128;
+// tiles of the tiled stage kernel (d = 1: 64 cells; d = 2: 16 x 16 cells)
+constexpr int kTile1X = 64;
+constexpr int kTile2X = 16, kTile2Y = 16;
 
 enum Field { F_Q0 = 0, F_Q1, F_Q2, F_QE, F_XH, F_NH, F_N1, F_N3, NFIELD };
 enum Kind { K_WALL = 0, K_LEAF = 1, K_FINER = 2, K_COARSER = 3 };
@@ -39,7 +42,9 @@ struct Grid {
     double* rf;
     int* leaves;
     int* inner;
-    int* counts;                    // [0..LMAX] leaves, [LMAX+1..] internal nodes
+    int* counts;                    // [0..LMAX] leaves, [LMAX+1..] internal nodes, [2(LMAX+1)..] active tiles
+    uint8_t* tflag;                 // per-level tile flags (tile holds a leaf), d <= 2
+    int* tlist;                     // per-level lists of active tiles, ascending
     double* scale;                  // [MMAX] detail normalisation s_v
     unsigned long long* scale_bits; // [MMAX] running max |q_v| (bit pattern)
     int* err;
@@ -52,6 +57,8 @@ struct Grid {
     int n[LMAX + 1];
     double dx[LMAX + 1][3];
     double rdx[LMAX + 1][3];        // 1 / dx
+    long long toff[LMAX + 1];       // tile offset of each level in tflag / tlist
+    int ntx[LMAX + 1], nty[LMAX + 1]; // tiles per direction
     int d, m, nf, L, lb, eq, rk, gts;
     int bc[3];
     double phys[8];
@@ -430,7 +437,10 @@ __device__ __forceinline__ double wave_speed(const Grid& g, const double* q)
 struct Launch; // fwd
 
 // kernel launchers (defined in the .cu files), all on stream `st`
-void launch_stage(const Grid& g, cudaStream_t st, int u, int s, int lmin, double dtl, double bw,
-                  int reg);
+// one compact RK stage s on every leaf of the levels lo..hi (independent
+// levels only), fine step dt (level u steps dt, or 2^{L-u} dt in LT mode),
+// RK weight b of the stage; returns the number of kernel launches issued
+int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt, double b,
+                 int reg);
 void launch_wave(const Grid& g, cudaStream_t st, int l);
 } // namespace mrlt

@@ -151,10 +151,13 @@ __global__ void __launch_bounds__(NTHREADS) k_stage(Grid g, int u, int s, int lm
     }
 }
 
-// Tile shapes of the tiled stage kernel: a CTA owns TX x TY cells of one level.
+// Tile shapes of the tiled stage kernel: a CTA owns TX x TY cells of one level
+// (the same shapes index the per-level active-tile lists).
 template <int D> struct Tile;
-template <> struct Tile<1> { static constexpr int TX = 64, TY = 1; };
-template <> struct Tile<2> { static constexpr int TX = 16, TY = 16; };
+template <> struct Tile<1> { static constexpr int TX = kTile1X, TY = 1; };
+template <> struct Tile<2> { static constexpr int TX = kTile2X, TY = kTile2Y; };
+// resident CTAs of a persistent stage launch (152 SMs x 3)
+constexpr long long kStageCtas = 456;
 
 // Append, in thread order, the items for which `take` holds to a shared list
 // (warp ballots and a block-wide prefix); every thread of the block calls it
@@ -193,7 +196,7 @@ __device__ __forceinline__ int block_append(bool take, int item, short* list, in
 // Work lists keep every warp on one kind of work.
 template <int EQ, int D>
 __global__ void __launch_bounds__(Tile<D>::TX * Tile<D>::TY)
-k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
+k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, int reg)
 {
     constexpr int M = EQ == 2 ? D + 2 : 1;
     constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, NT = TX * TY, H = 2;
@@ -209,10 +212,30 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
     __shared__ short sList[NL];
     __shared__ int sWarp[NT / 32];
 
+    // The CTA walks the active tiles (tiles holding a leaf) of levels lo..hi,
+    // in level order; one launch may cover several independent levels.
+    __shared__ int sBase[LMAX + 2];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = lo; l <= hi; ++l) {
+            sBase[l - lo] = acc;
+            acc += g.counts[2 * (LMAX + 1) + l];
+        }
+        sBase[hi - lo + 1] = acc;
+    }
+    __syncthreads();
+    const int ntask = sBase[hi - lo + 1];
+    for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+    int li = 0;
+    while (task >= sBase[li + 1]) ++li;
+    const int u = lo + li;
+    const int tile = g.tlist[g.toff[u] + task - sBase[li]];
+    const double dtl = g.gts ? dt : ldexp(dt, g.L - u); // Eq. 13 step of level u
+    const double bw = dtl * bstage; // register weight dt_l b_s
     const int n = g.n[u];
     const int ntx = (n + TX - 1) / TX;
-    const int ox = (blockIdx.x % ntx) * TX;
-    const int oy = D > 1 ? (blockIdx.x / ntx) * TY : 0;
+    const int ox = (tile % ntx) * TX;
+    const int oy = D > 1 ? (tile / ntx) * TY : 0;
     const int tid = threadIdx.x;
     const Ctx x{u, s, lmin};
     const bool finer = u < g.L; // internal nodes of level u have children
@@ -274,7 +297,7 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
     }
     __syncthreads();
     const int nleaf = __syncthreads_count(tile_leaf(H + tid % TX, D > 1 ? H + tid / TX : 0));
-    if (nleaf == 0) return;
+    if (nleaf == 0) continue; // uniform across the CTA
     if (tid == 0) {
         if (s == 1) atomicAdd(g.updates, (unsigned long long)nleaf);
         atomicAdd(&g.work[u * 4 + s], (unsigned long long)nleaf);
@@ -420,7 +443,7 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
     {
         const int i = tid % TX, j = D > 1 ? tid / TX : 0;
         const int bx = H + i, by = D > 1 ? H + j : 0, b = by * BX + bx;
-        if (!tile_leaf(bx, by)) return;
+        if (tile_leaf(bx, by)) {
         const long long id = cell_id(g, u, ox + i, oy + j, 0);
         double self[M], f[M];
 #pragma unroll
@@ -449,6 +472,9 @@ k_stage_tile(Grid g, int u, int s, int lmin, double dtl, double bw, int reg)
             }
         }
         rk_update<M>(g, u, id, s, dtl, f);
+        }
+    }
+    __syncthreads(); // shared arrays are reused by the next tile
     }
 }
 
@@ -484,27 +510,34 @@ static int grid_for(const Grid& g, int l)
 }
 
 template <int EQ, int D>
-static void stage_dispatch(const Grid& g, cudaStream_t st, int u, int s, int lmin, double dtl,
-                           double bw, int reg)
+static int stage_dispatch(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt,
+                          double b, int reg)
 {
     if constexpr (D <= 2) {
-        const long long ntx = (g.n[u] + Tile<D>::TX - 1) / Tile<D>::TX;
-        const long long tiles = D == 1 ? ntx : ntx * ((g.n[u] + Tile<D>::TY - 1) / Tile<D>::TY);
-        k_stage_tile<EQ, D><<<(unsigned)tiles, Tile<D>::TX * Tile<D>::TY, 0, st>>>(g, u, s, lmin, dtl, bw, reg);
+        long long total = 0;
+        for (int l = lo; l <= hi; ++l) total += (long long)g.ntx[l] * g.nty[l];
+        const long long grid = total < kStageCtas ? total : kStageCtas;
+        k_stage_tile<EQ, D><<<(unsigned)grid, Tile<D>::TX * Tile<D>::TY, 0, st>>>(g, lo, hi, s, lmin, dt, b, reg);
+        return 1;
     } else {
-        k_stage<EQ, D><<<grid_for(g, u), NTHREADS, 0, st>>>(g, u, s, lmin, dtl, bw, reg);
+        for (int u = lo; u <= hi; ++u) {
+            const double dtl = g.gts ? dt : ldexp(dt, g.L - u);
+            k_stage<EQ, D><<<grid_for(g, u), NTHREADS, 0, st>>>(g, u, s, lmin, dtl, dtl * b, reg);
+        }
+        return hi - lo + 1;
     }
 }
 
-void launch_stage(const Grid& g, cudaStream_t st, int u, int s, int lmin, double dtl, double bw, int reg)
+int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt, double b, int reg)
 {
 #define MRLT_CASE(E, DD) \
-    if (g.eq == E && g.d == DD) return stage_dispatch<E, DD>(g, st, u, s, lmin, dtl, bw, reg);
+    if (g.eq == E && g.d == DD) return stage_dispatch<E, DD>(g, st, lo, hi, s, lmin, dt, b, reg);
     MRLT_CASE(0, 1) MRLT_CASE(0, 2) MRLT_CASE(0, 3)
     MRLT_CASE(1, 1) MRLT_CASE(1, 2) MRLT_CASE(1, 3)
     MRLT_CASE(2, 1) MRLT_CASE(2, 2) MRLT_CASE(2, 3)
     MRLT_CASE(3, 1) MRLT_CASE(3, 2) MRLT_CASE(3, 3)
 #undef MRLT_CASE
+    return 0;
 }
 
 void launch_wave(const Grid& g, cudaStream_t st, int l)

@@ -22,21 +22,23 @@ static inline int blocks_list(const Grid& g, int l)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
 // ------------------------------------------------------------ simple leaf copies
-__global__ void k_leaf_copy(Grid g, int l, int from, int to)
+__global__ void k_leaf_copy(Grid g, int lo, int hi, int from, int to)
 {
-    const int cnt = g.counts[l];
-    const int* list = g.leaves + g.off[l];
-    const long long N = g.N[l];
-    const double* a = fbase(g, from, l);
-    double* b = fbase_w(g, to, l);
-    GRID_STRIDE(t, cnt)
-    {
-        const long long id = list[t];
-        if (id < 0 || id >= N) {
-            atomicOr(g.err, ERR_INDEX);
-            continue;
+    for (int l = lo; l <= hi; ++l) {
+        const int cnt = g.counts[l];
+        const int* list = g.leaves + g.off[l];
+        const long long N = g.N[l];
+        const double* a = fbase(g, from, l);
+        double* b = fbase_w(g, to, l);
+        GRID_STRIDE(t, cnt)
+        {
+            const long long id = list[t];
+            if (id < 0 || id >= N) {
+                atomicOr(g.err, ERR_INDEX);
+                continue;
+            }
+            for (int v = 0; v < g.m; ++v) b[v * N + id] = a[v * N + id];
         }
-        for (int v = 0; v < g.m; ++v) b[v * N + id] = a[v * N + id];
     }
 }
 
@@ -434,6 +436,36 @@ __global__ void k_cmp_scatter(Grid g, int l, const int* bc)
     const unsigned below = (1u << lane) - 1u;
     if (s == 1) g.leaves[g.off[l] + wl[warp] + __popc(bl & below)] = (int)i;
     if (s == 2) g.inner[g.off[l] + wi[warp] + __popc(bi & below)] = (int)i;
+    if (s == 1 && g.d <= 2) { // the leaf's tile is active
+        const int n = g.n[l];
+        const int tx = g.d == 1 ? kTile1X : kTile2X;
+        const long long x = i % n, y = g.d == 2 ? i / n : 0;
+        g.tflag[g.toff[l] + x / tx + (long long)g.ntx[l] * (y / kTile2Y)] = 1;
+    }
+}
+
+// ordered list of the active tiles of level l (single block)
+__global__ void k_tile_list(Grid g, int l)
+{
+    __shared__ int sc[1024];
+    const int nt = g.ntx[l] * g.nty[l];
+    const uint8_t* fl = g.tflag + g.toff[l];
+    const int tid = threadIdx.x, per = (nt + 1023) / 1024;
+    const int t0 = tid * per, t1 = min(t0 + per, nt);
+    int c = 0;
+    for (int t = t0; t < t1; ++t) c += fl[t] != 0;
+    sc[tid] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int xo = tid >= o ? sc[tid - o] : 0;
+        __syncthreads();
+        sc[tid] += xo;
+        __syncthreads();
+    }
+    int pos = sc[tid] - c;
+    for (int t = t0; t < t1; ++t)
+        if (fl[t]) g.tlist[g.toff[l] + pos++] = t;
+    if (tid == 1023) g.counts[2 * (LMAX + 1) + l] = sc[1023];
 }
 
 // ------------------------------------------------------------ registers
@@ -441,8 +473,9 @@ __global__ void k_cmp_scatter(Grid g, int l, const int* bc)
 // q += +-(coarse time-integrated flux - mean of the fine ones) / dx; the
 // registers read are cleared for the next step
 template <int D>
-__global__ void k_reflux(Grid g, int l)
+__global__ void k_reflux(Grid g, int lo, int hi)
 {
+  for (int l = lo; l <= hi; ++l) {
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
     const long long N = g.N[l], Nf = g.N[l + 1];
@@ -494,6 +527,7 @@ __global__ void k_reflux(Grid g, int l)
             }
         }
     }
+  }
 }
 
 // ------------------------------------------------------------ reductions
@@ -652,10 +686,10 @@ void Launcher::project(int l, int mode)
     else project_d<3>(*this, l, mode);
 }
 
-void Launcher::leaf_copy(int l, int from, int to)
+void Launcher::leaf_copy(int lo, int hi, int from, int to)
 {
     ++n;
-    k_leaf_copy<<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l, from, to);
+    k_leaf_copy<<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi, from, to);
 }
 
 template <int D, int M>
@@ -691,18 +725,23 @@ void Launcher::apply_tree(int la) { MRLT_DM_DISPATCH(apply_dm, *this, la); }
 void Launcher::compact(int l)
 {
     const int nb = (int)((g.N[l] + NTHREADS - 1) / NTHREADS);
+    if (g.d <= 2) cudaMemsetAsync(g.tflag + g.toff[l], 0, (size_t)g.ntx[l] * g.nty[l], st);
     k_cmp_count<<<nb, NTHREADS, 0, st>>>(g, l, bc);
     k_cmp_scan<<<1, 1024, 0, st>>>(nb, bc, g.counts, l);
     k_cmp_scatter<<<nb, NTHREADS, 0, st>>>(g, l, bc);
     n += 3;
+    if (g.d <= 2) {
+        k_tile_list<<<1, 1024, 0, st>>>(g, l);
+        ++n;
+    }
 }
 
-void Launcher::reflux(int l)
+void Launcher::reflux(int lo, int hi)
 {
     ++n;
-    if (g.d == 1) k_reflux<1><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
-    else if (g.d == 2) k_reflux<2><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
-    else k_reflux<3><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
+    if (g.d == 1) k_reflux<1><<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi);
+    else if (g.d == 2) k_reflux<2><<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi);
+    else k_reflux<3><<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi);
 }
 
 void Launcher::scale(int l)

@@ -14,11 +14,11 @@ struct Launcher {
     long long n = 0;   // kernel launches issued
 
     void project(int l, int mode);
-    void leaf_copy(int l, int from, int to);
+    void leaf_copy(int lo, int hi, int from, int to); // leaves of levels lo..hi
     void mark_refinements(int la);
     void apply_tree(int la);
     void compact(int l);
-    void reflux(int l);
+    void reflux(int lo, int hi);                       // coarse levels lo..hi
     void scale(int l);
     void finite(int l);
     void mass(int l, double* part);
