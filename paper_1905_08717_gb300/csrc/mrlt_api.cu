@@ -170,7 +170,7 @@ mr_status adapt(mr_solver* h, int la)
     MR_CK(cudaMemsetAsync(g.flag + g.off[la], 0, (size_t)(h->ntot - g.off[la]), h->stream));
     h->K.mark_refinements(la);
     h->K.apply_tree(la);
-    for (int l = la; l <= g.L; ++l) h->K.compact(l);
+    h->K.compact(la, g.L);
     for (int l = g.L - 1; l >= la; --l) h->K.project(l, PM_Q0);
     return MR_OK;
 }
@@ -297,7 +297,7 @@ mr_status init_state(mr_solver* h, const double* q0)
                           cudaMemcpyHostToDevice, h->stream));
     for (int l = g.lb; l <= g.L; ++l)
         MR_CK(cudaMemsetAsync(g.st + g.off[l], l < g.L ? 2 : 1, (size_t)g.N[l], h->stream));
-    for (int l = g.lb; l <= g.L; ++l) h->K.compact(l);
+    h->K.compact(g.lb, g.L);
     for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
     if (h->cfg.adapt_mode != MR_ADAPT_NEVER) MR_TRY(adapt(h, g.lb));
     h->K.leaf_copy(g.lb, g.L, F_Q0, F_QE);
@@ -376,7 +376,9 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     A(dev_alloc(h, &g.work, (LMAX + 1) * 4));
     if (r == MR_OK && cudaMemset(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long)) != cudaSuccess)
         r = MR_E_CUDA; // cumulative counters: never cleared by mr_reset
-    A(dev_alloc(h, &h->K.bc, 2 * ((g.N[g.L] + NTHREADS - 1) / NTHREADS)));
+    long long nblk = 0;
+    for (int l = g.lb; l <= g.L; ++l) nblk += (g.N[l] + NTHREADS - 1) / NTHREADS;
+    A(dev_alloc(h, &h->K.bc, 2 * nblk));
     A(dev_alloc(h, &h->d_part, (size_t)(LMAX + 1) * MASS_BLOCKS * g.m));
     A(dev_alloc(h, &h->d_T, nd));
     A(dev_alloc(h, &h->d_us, off));
@@ -476,7 +478,7 @@ mr_status mr_set_tree(mr_solver* h, const unsigned char* lev)
             if (R[l][id]) fl[g.off[l] + id] = FL_REF;
     MR_CK(cudaMemcpyAsync(g.flag, fl.data(), fl.size(), cudaMemcpyHostToDevice, h->stream));
     h->K.apply_tree(lb);
-    for (int l = lb; l <= L; ++l) h->K.compact(l);
+    h->K.compact(lb, L);
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
     h->K.leaf_copy(lb, L, F_Q0, F_QE);
     return sync_check(h);

@@ -145,51 +145,53 @@ __device__ __forceinline__ double eps_level(const Grid& g, int l)
     return g.eps_mode == 1 ? ldexp(g.eps, g.d * (l - g.L)) : g.eps;
 }
 
-// detail norm (Eq. 5) of every internal node of level l: max over children
-// and variables of |q_child - prediction| / s_v; flags significance (> eps_{l+1})
-// and the scale-safety bound (> 8 eps_{l+1})
+// detail norm (Eq. 5) of every internal node of levels lo..hi (< L): max over
+// children and variables of |q_child - prediction| / s_v; flags significance
+// (> eps_{l+1}) and the scale-safety bound (> 8 eps_{l+1})
 template <int D, int M>
-__global__ void k_detail(Grid g, int l)
+__global__ void k_detail(Grid g, int lo, int hi)
 {
-    const int cnt = g.counts[LMAX + 1 + l];
-    const int* list = g.inner + g.off[l];
-    const long long N = g.N[l], Nc = g.N[l + 1];
-    const double el = eps_level(g, l + 1);
     double sc[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) sc[v] = __longlong_as_double((long long)g.scale_bits[v]);
-    GRID_STRIDE(t, cnt)
-    {
-        const long long id = list[t];
-        if (id < 0 || id >= N) {
-            atomicOr(g.err, ERR_INDEX);
-            continue;
-        }
-        uint8_t fl = 0;
-        if (g.eps <= 0.0) {
-            fl = FL_SIG;
-        } else {
-            int c[3];
-            cell_xyz(g, l, id, c);
-            const Ctx x{l, 0, g.lb};
-            double nrm = 0.0;
-#pragma unroll 1
-            for (int k = 0; k < (1 << D); ++k) {
-                int q[3] = {2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
-                            D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0};
-                double p[M];
-                predict<D, M>(g, x, l + 1, q, p);
-                const long long cid = cell_id(g, l + 1, q[0], q[1], q[2]);
-                const double* qc = fbase(g, F_Q0, l + 1) + cid;
-#pragma unroll
-                for (int v = 0; v < M; ++v) nrm = fmax(nrm, fabs(qc[v * Nc] - p[v]) / sc[v]);
+    for (int l = lo; l <= hi; ++l) {
+        const int cnt = g.counts[LMAX + 1 + l];
+        const int* list = g.inner + g.off[l];
+        const long long N = g.N[l], Nc = g.N[l + 1];
+        const double el = eps_level(g, l + 1);
+        GRID_STRIDE(t, cnt)
+        {
+            const long long id = list[t];
+            if (id < 0 || id >= N) {
+                atomicOr(g.err, ERR_INDEX);
+                continue;
             }
-            if (fabs(nrm - el) <= 1e-10 * el || fabs(nrm - 8.0 * el) <= 8e-10 * el)
-                atomicAdd(g.near, 1ull);
-            if (nrm > el) fl |= FL_SIG;
-            if (nrm > 8.0 * el) fl |= FL_BIG;
+            uint8_t fl = 0;
+            if (g.eps <= 0.0) {
+                fl = FL_SIG;
+            } else {
+                int c[3];
+                cell_xyz(g, l, id, c);
+                const Ctx x{l, 0, g.lb};
+                double nrm = 0.0;
+#pragma unroll 1
+                for (int k = 0; k < (1 << D); ++k) {
+                    int q[3] = {2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
+                                D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0};
+                    double p[M];
+                    predict<D, M>(g, x, l + 1, q, p);
+                    const long long cid = cell_id(g, l + 1, q[0], q[1], q[2]);
+                    const double* qc = fbase(g, F_Q0, l + 1) + cid;
+#pragma unroll
+                    for (int v = 0; v < M; ++v) nrm = fmax(nrm, fabs(qc[v * Nc] - p[v]) / sc[v]);
+                }
+                if (fabs(nrm - el) <= 1e-10 * el || fabs(nrm - 8.0 * el) <= 8e-10 * el)
+                    atomicAdd(g.near, 1ull);
+                if (nrm > el) fl |= FL_SIG;
+                if (nrm > 8.0 * el) fl |= FL_BIG;
+            }
+            g.flag[g.off[l] + id] |= fl;
         }
-        g.flag[g.off[l] + id] |= fl;
     }
 }
 
@@ -209,62 +211,88 @@ __device__ __forceinline__ bool nb3(const Grid& g, int l, const int c[3], int dx
         for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) \
             for (int dx = -1; dx <= 1; ++dx)
 
-// desired refinement of level l: significant node in the 3^d neighbourhood
-// (space safety), or parent flagged by scale safety; eps = 0 refines all
+// desired refinement of levels lo..hi: significant node in the 3^d
+// neighbourhood (space safety), or parent flagged by scale safety (parent
+// level >= la); eps = 0 refines all
 template <int D>
-__global__ void k_desire(Grid g, int l, int la)
+__global__ void k_desire(Grid g, int lo, int hi, int la)
 {
-    const long long N = g.N[l];
-    uint8_t* fl = g.flag + g.off[l];
-    GRID_STRIDE(id, N)
-    {
-        bool want = g.eps <= 0.0;
-        if (!want) {
-            int c[3];
-            cell_xyz(g, l, id, c);
-            FOR3(D, dx, dy, dz)
-            {
-                long long j;
-                if (nb3<D>(g, l, c, dx, dy, dz, &j) && (fl[j] & FL_SIG)) want = true;
+    for (int l = lo; l <= hi; ++l) {
+        const long long N = g.N[l];
+        uint8_t* fl = g.flag + g.off[l];
+        GRID_STRIDE(id, N)
+        {
+            bool want = g.eps <= 0.0;
+            if (!want) {
+                int c[3];
+                cell_xyz(g, l, id, c);
+                FOR3(D, dx, dy, dz)
+                {
+                    long long j;
+                    if (nb3<D>(g, l, c, dx, dy, dz, &j) && (fl[j] & FL_SIG)) want = true;
+                }
+                if (!want && l - 1 >= la) {
+                    const long long p = cell_id(g, l - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1);
+                    if (g.flag[g.off[l - 1] + p] & FL_BIG) want = true;
+                }
             }
-            if (!want && l - 1 >= la) {
-                const long long p = cell_id(g, l - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1);
-                if (g.flag[g.off[l - 1] + p] & FL_BIG) want = true;
-            }
+            if (want) fl[id] |= FL_DES;
         }
-        if (want) fl[id] |= FL_DES;
     }
 }
 
-// admissible refinements at level l (top-down): every node of level l-1 that
-// the grading rule would require is refined already (frozen level la-1) or
-// admissible itself; R = desired and admissible
+// Admissible refinements of levels lo..hi and R = desired and admissible.
+// A node (l, i) may be refined if every node of the frozen level la-1 its
+// grading chain requires is refined already.  Unrolling the rule "refining
+// (m, j) needs (m-1, floor(j/2) + delta), |delta| <= 1" from level l down to
+// la-1 gives, per direction, the interval [a, b] obtained by
+// a -> floor(a/2) - 1, b -> floor(b/2) + 1 (l - la + 1 times), wrapped when
+// periodic and clipped at walls.  At a full adaptation (la = min level)
+// everything is admissible.
 template <int D>
-__global__ void k_allow(Grid g, int l, int la)
+__global__ void k_allow(Grid g, int lo, int hi, int la)
 {
-    const long long N = g.N[l];
-    uint8_t* fl = g.flag + g.off[l];
-    GRID_STRIDE(id, N)
-    {
-        bool ok = true;
-        if (!(l == la && la == g.lb)) {
-            int c[3];
-            cell_xyz(g, l, id, c);
-            const int P[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
-            FOR3(D, dx, dy, dz)
-            {
-                long long j;
-                if (!nb3<D>(g, l - 1, P, dx, dy, dz, &j)) continue;
-                if (l - 1 < la) ok = ok && status(g, l - 1, j) == 2;
-                else ok = ok && (g.flag[g.off[l - 1] + j] & FL_ALLOW);
+    for (int l = lo; l <= hi; ++l) {
+        const long long N = g.N[l];
+        uint8_t* fl = g.flag + g.off[l];
+        GRID_STRIDE(id, N)
+        {
+            bool ok = true;
+            if (la > g.lb) {
+                int c[3];
+                cell_xyz(g, l, id, c);
+                const int pl = la - 1, n = g.n[pl];
+                int lo3[3] = {0, 0, 0}, cnt3[3] = {1, 1, 1};
+                for (int k = 0; k < D; ++k) {
+                    int a = c[k], b = c[k];
+                    for (int m = l; m >= la; --m) {
+                        a = (a >> 1) - 1; // arithmetic shift: floor for negatives
+                        b = (b >> 1) + 1;
+                    }
+                    if (g.bc[k] == 0) {
+                        lo3[k] = a;
+                        cnt3[k] = min(b - a + 1, n);
+                    } else {
+                        lo3[k] = max(a, 0);
+                        cnt3[k] = min(b, n - 1) - lo3[k] + 1;
+                    }
+                }
+                for (int tz = 0; tz < cnt3[2] && ok; ++tz)
+                    for (int ty = 0; ty < cnt3[1] && ok; ++ty)
+                        for (int tx = 0; tx < cnt3[0] && ok; ++tx) {
+                            int q[3] = {lo3[0] + tx, lo3[1] + ty, lo3[2] + tz};
+                            for (int k = 0; k < D; ++k)
+                                if (g.bc[k] == 0) q[k] = ((q[k] % n) + n) % n;
+                            ok = status(g, pl, cell_id(g, pl, q[0], q[1], q[2])) == 2;
+                        }
             }
+            uint8_t f = fl[id];
+            if (ok) {
+                f |= FL_ALLOW;
+                if (f & FL_DES) f |= FL_REF;
+            }
+            fl[id] = f;
         }
-        uint8_t f = fl[id];
-        if (ok) {
-            f |= FL_ALLOW;
-            if (f & FL_DES) f |= FL_REF;
-        }
-        fl[id] = f;
     }
 }
 
@@ -346,10 +374,25 @@ __global__ void k_apply(Grid g, int l, int la)
 }
 
 // ------------------------------------------------------------ compaction
-__global__ void k_cmp_count(Grid g, int l, int* bc)
+// Level l owns the blocks [lb.base[l], lb.base[l+1]) of a compaction launch
+// over levels lb.lo..lb.hi (NTHREADS cells per block).
+struct LevelBlocks {
+    int lo, hi;
+    int base[LMAX + 2];
+};
+
+__device__ __forceinline__ int block_level(const LevelBlocks& b, int blk)
 {
+    int l = b.lo;
+    while (l < b.hi && blk >= b.base[l + 1]) ++l;
+    return l;
+}
+
+__global__ void k_cmp_count(Grid g, LevelBlocks lbk, int* bc)
+{
+    const int l = block_level(lbk, blockIdx.x);
     const long long N = g.N[l];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = (long long)(blockIdx.x - lbk.base[l]) * blockDim.x + threadIdx.x;
     const int s = i < N ? status(g, l, i) : 0;
     const unsigned bl = __ballot_sync(0xffffffffu, s == 1);
     const unsigned bi = __ballot_sync(0xffffffffu, s == 2);
@@ -371,13 +414,15 @@ __global__ void k_cmp_count(Grid g, int l, int* bc)
     }
 }
 
-// exclusive scan of the per-block counts (single block), totals to counts[l]
-__global__ void k_cmp_scan(int nb, int* bc, int* counts, int l)
+// exclusive scan of the per-block counts, one block per level; totals to counts[l]
+__global__ void k_cmp_scan(Grid g, LevelBlocks lbk, int* bc)
 {
     __shared__ int sa[1024], sb[1024];
+    const int l = lbk.lo + blockIdx.x;
+    const int b0l = lbk.base[l], nb = lbk.base[l + 1] - b0l;
     const int tid = threadIdx.x;
     const int per = (nb + 1023) / 1024;
-    const int b0 = tid * per, b1 = min(b0 + per, nb);
+    const int b0 = b0l + tid * per, b1 = min(b0 + per, b0l + nb);
     int a = 0, b = 0;
     for (int i = b0; i < b1; ++i) {
         a += bc[2 * i];
@@ -403,15 +448,16 @@ __global__ void k_cmp_scan(int nb, int* bc, int* counts, int l)
         eb += tb;
     }
     if (tid == 1023) {
-        counts[l] = sa[1023];
-        counts[LMAX + 1 + l] = sb[1023];
+        g.counts[l] = sa[1023];
+        g.counts[LMAX + 1 + l] = sb[1023];
     }
 }
 
-__global__ void k_cmp_scatter(Grid g, int l, const int* bc)
+__global__ void k_cmp_scatter(Grid g, LevelBlocks lbk, const int* bc)
 {
+    const int l = block_level(lbk, blockIdx.x);
     const long long N = g.N[l];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = (long long)(blockIdx.x - lbk.base[l]) * blockDim.x + threadIdx.x;
     const int s = i < N ? status(g, l, i) : 0;
     const unsigned bl = __ballot_sync(0xffffffffu, s == 1);
     const unsigned bi = __ballot_sync(0xffffffffu, s == 2);
@@ -444,10 +490,11 @@ __global__ void k_cmp_scatter(Grid g, int l, const int* bc)
     }
 }
 
-// ordered list of the active tiles of level l (single block)
-__global__ void k_tile_list(Grid g, int l)
+// ordered list of the active tiles of level lo + blockIdx.x (one block per level)
+__global__ void k_tile_list(Grid g, int lo)
 {
     __shared__ int sc[1024];
+    const int l = lo + blockIdx.x;
     const int nt = g.ntx[l] * g.nty[l];
     const uint8_t* fl = g.tflag + g.toff[l];
     const int tid = threadIdx.x, per = (nt + 1023) / 1024;
@@ -696,9 +743,11 @@ template <int D, int M>
 static void adapt_dm(Launcher& L, int la)
 {
     const Grid& g = L.g;
-    for (int l = la; l < g.L; ++l, ++L.n) k_detail<D, M><<<blocks_list(g, l), NTHREADS, 0, L.st>>>(g, l);
-    for (int l = la; l < g.L; ++l, ++L.n) k_desire<D><<<blocks_dense(g.N[l]), NTHREADS, 0, L.st>>>(g, l, la);
-    for (int l = la; l < g.L; ++l, ++L.n) k_allow<D><<<blocks_dense(g.N[l]), NTHREADS, 0, L.st>>>(g, l, la);
+    const int hi = g.L - 1; // levels whose nodes may own children
+    k_detail<D, M><<<blocks_list(g, hi), NTHREADS, 0, L.st>>>(g, la, hi);
+    k_desire<D><<<blocks_dense(g.N[hi]), NTHREADS, 0, L.st>>>(g, la, hi, la);
+    k_allow<D><<<blocks_dense(g.N[hi]), NTHREADS, 0, L.st>>>(g, la, hi, la);
+    L.n += 3;
     for (int l = g.L - 1; l > la; --l, ++L.n) k_close<D><<<blocks_dense(g.N[l - 1]), NTHREADS, 0, L.st>>>(g, l);
 }
 
@@ -722,16 +771,24 @@ static void apply_dm(Launcher& L, int la)
 void Launcher::mark_refinements(int la) { MRLT_DM_DISPATCH(adapt_dm, *this, la); }
 void Launcher::apply_tree(int la) { MRLT_DM_DISPATCH(apply_dm, *this, la); }
 
-void Launcher::compact(int l)
+void Launcher::compact(int lo, int hi)
 {
-    const int nb = (int)((g.N[l] + NTHREADS - 1) / NTHREADS);
-    if (g.d <= 2) cudaMemsetAsync(g.tflag + g.toff[l], 0, (size_t)g.ntx[l] * g.nty[l], st);
-    k_cmp_count<<<nb, NTHREADS, 0, st>>>(g, l, bc);
-    k_cmp_scan<<<1, 1024, 0, st>>>(nb, bc, g.counts, l);
-    k_cmp_scatter<<<nb, NTHREADS, 0, st>>>(g, l, bc);
+    LevelBlocks lbk;
+    lbk.lo = lo;
+    lbk.hi = hi;
+    int total = 0;
+    for (int l = lo; l <= hi; ++l) {
+        lbk.base[l] = total;
+        total += (int)((g.N[l] + NTHREADS - 1) / NTHREADS);
+    }
+    lbk.base[hi + 1] = total;
+    if (g.d <= 2) cudaMemsetAsync(g.tflag + g.toff[lo], 0, (size_t)(g.toff[hi] - g.toff[lo]) + (size_t)g.ntx[hi] * g.nty[hi], st);
+    k_cmp_count<<<total, NTHREADS, 0, st>>>(g, lbk, bc);
+    k_cmp_scan<<<hi - lo + 1, 1024, 0, st>>>(g, lbk, bc);
+    k_cmp_scatter<<<total, NTHREADS, 0, st>>>(g, lbk, bc);
     n += 3;
     if (g.d <= 2) {
-        k_tile_list<<<1, 1024, 0, st>>>(g, l);
+        k_tile_list<<<hi - lo + 1, 1024, 0, st>>>(g, lo);
         ++n;
     }
 }

@@ -10,14 +10,14 @@ constexpr int MASS_BLOCKS = 64;
 struct Launcher {
     Grid g;
     cudaStream_t st = nullptr;
-    int* bc = nullptr; // compaction scratch, 2 ints per block of the largest level
+    int* bc = nullptr; // compaction scratch, 2 ints per block over all levels
     long long n = 0;   // kernel launches issued
 
     void project(int l, int mode);
     void leaf_copy(int lo, int hi, int from, int to); // leaves of levels lo..hi
     void mark_refinements(int la);
     void apply_tree(int la);
-    void compact(int l);
+    void compact(int lo, int hi);                      // leaf / node / tile lists of levels lo..hi
     void reflux(int lo, int hi);                       // coarse levels lo..hi
     void scale(int l);
     void finite(int l);
