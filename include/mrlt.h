@@ -50,6 +50,11 @@ enum { MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_EULER = 2, MR_EQ_REACTION_D
 enum { MR_BC_PERIODIC = 0, MR_BC_NEUMANN = 1 };
 enum { MR_TIME_GTS = 0, MR_TIME_LT_NERK = 1 };
 enum { MR_ADAPT_NEVER = 0, MR_ADAPT_MACRO = 1, MR_ADAPT_EVERY = 2 };
+/* Arithmetic of the stage kernels.  MR_PREC_MIXED evaluates the MUSCL
+ * reconstruction and the numerical face fluxes in FP32; the stored cell
+ * averages, the RK updates, the flux registers, the CFL reduction and the whole
+ * adaptation (details, thresholds, prediction, projection) stay FP64. */
+enum { MR_PREC_FP64 = 0, MR_PREC_MIXED = 1 };
 
 /* Problem statement (Sec. 2, Eq. 1) and the method's parameters. */
 typedef struct mr_config {
@@ -64,7 +69,7 @@ typedef struct mr_config {
     int    eps_mode;   /* 0: eps on every level; 1: eps_l = 2^{d (l-L)} eps          */
     int    rk_order;   /* 2 or 3: compact RK2/RK3 of Sec. 3                          */
     int    time_mode;  /* MR_TIME_GTS (all leaves step dt) or MR_TIME_LT_NERK       */
-    int    precision;  /* 0 = FP64 (the only value accepted)                        */
+    int    precision;  /* MR_PREC_FP64 or MR_PREC_MIXED                              */
     int    adapt_mode; /* MR_ADAPT_*: never (fixed tree), at each macro-step start,
                           or at every LT iteration on the synchronised levels      */
     int    reflux;     /* 1: conservative flux registers at coarse-fine faces (LT)  */

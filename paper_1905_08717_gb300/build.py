@@ -13,8 +13,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "libmrlt.so")
-SOURCES = ["mrlt_api.cu", "mrlt_tree.cu", "mrlt_stage.cu", "mrlt_noalloc.cu"]
-HEADERS = ["mrlt_impl.cuh", "mrlt_tree.cuh"]
+# (source, extra flags, object tag): the stage kernels are compiled once per
+# equation so that the heaviest translation units build in parallel
+UNITS = [("mrlt_api.cu", [], "api"), ("mrlt_tree.cu", [], "tree"), ("mrlt_stage.cu", [], "stage"),
+         ("mrlt_noalloc.cu", [], "noalloc")] + [
+            ("mrlt_stage_eq.cu", [f"-DMRLT_STAGE_EQ={e}"], f"stage_eq{e}") for e in range(4)]
+SOURCES = sorted({u[0] for u in UNITS})
+HEADERS = ["mrlt_impl.cuh", "mrlt_tree.cuh", "mrlt_stage.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]
@@ -39,9 +44,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     objs, procs = [], []
-    for src in SOURCES:
-        obj = os.path.join(CSRC, src.replace(".cu", f".{os.getpid()}.o"))
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+    for src, extra, tag in UNITS:
+        obj = os.path.join(CSRC, f"{tag}.{os.getpid()}.o")
+        cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         procs.append((subprocess.Popen(cmd), cmd))

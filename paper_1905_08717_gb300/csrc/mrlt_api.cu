@@ -66,7 +66,7 @@ mr_status validate(const mr_config* c)
     if (c->equation < 0 || c->equation > 3) return MR_E_INVALID;
     if (c->rk_order != 2 && c->rk_order != 3) return MR_E_INVALID;
     if (c->time_mode != MR_TIME_GTS && c->time_mode != MR_TIME_LT_NERK) return MR_E_INVALID;
-    if (c->precision != 0) return MR_E_INVALID;
+    if (c->precision != MR_PREC_FP64 && c->precision != MR_PREC_MIXED) return MR_E_INVALID;
     if (c->adapt_mode < 0 || c->adapt_mode > 2) return MR_E_INVALID;
     if (!(c->cfl > 0.0) || !(c->eps >= 0.0)) return MR_E_INVALID;
     for (int k = 0; k < c->dim; ++k) {
@@ -334,6 +334,7 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     for (int k = 0; k < 8; ++k) g.phys[k] = cfg->phys[k];
     g.eps = cfg->eps;
     g.eps_mode = cfg->eps_mode;
+    g.prec = cfg->precision;
     long long off = 0, toff = 0;
     for (int l = g.lb; l <= g.L; ++l) {
         g.toff[l] = toff;

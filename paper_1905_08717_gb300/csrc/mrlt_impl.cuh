@@ -64,6 +64,7 @@ struct Grid {
     double phys[8];
     double eps;
     int eps_mode;
+    int prec;                       // 0 FP64, 1 mixed: face fluxes in FP32
 };
 
 // exposure context: level u being updated, stage s (0 = plain q^n), lmin
@@ -253,11 +254,13 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
     }
     const int P0 = q[0] >> 1, P1 = q[1] >> 1, P2 = q[2] >> 1;
     const int a0 = q[0] & 1, a1 = q[1] & 1, a2 = q[2] & 1;
-#pragma unroll
+    // in 3D the outer loops stay rolled: 27 inlined exposures per prediction
+    // site cost far more compile time than the loop overhead they save
+#pragma unroll(D > 2 ? 1 : 3)
     for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
         const int z = D > 2 ? wrap_or_mirror(g, pl, 2, P2 + dz) : 0;
         const double wz = D > 2 ? pw(a2, dz) : 1.0;
-#pragma unroll
+#pragma unroll(D > 2 ? 1 : 3)
         for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
             const int y = D > 1 ? wrap_or_mirror(g, pl, 1, P1 + dy) : 0;
             const double wyz = wz * (D > 1 ? pw(a1, dy) : 1.0);
@@ -294,62 +297,66 @@ __device__ __forceinline__ void value_at(const Grid& g, const Ctx& x, int l, con
 }
 
 // ---------------------------------------------------------------- physics
-__device__ __forceinline__ double minmod(double a, double b)
+template <class R>
+__device__ __forceinline__ R minmod(R a, R b)
 {
-    if (a * b <= 0.0) return 0.0;
+    if (a * b <= R(0)) return R(0);
     return fabs(a) < fabs(b) ? a : b;
 }
 
 // Variables that MUSCL reconstructs: primitives (rho, u_1..u_d, p) for Euler,
-// the conserved variable itself otherwise.
-template <int EQ, int D, int M>
-__device__ __forceinline__ void recon_vars(const Grid& g, const double* W, double* P)
+// the conserved variable itself otherwise.  R is the arithmetic type of the
+// flux evaluation: double, or float in the mixed-precision mode (the stored
+// state W stays double in both).
+template <int EQ, int D, int M, class R>
+__device__ __forceinline__ void recon_vars(const Grid& g, const double* W, R* P)
 {
     if constexpr (EQ == 2) {
-        const double gam = g.phys[0];
-        const double rho = W[0];
-        const double ir = 1.0 / rho;
-        double ke = 0.0;
+        const R gam = R(g.phys[0]);
+        const R rho = R(W[0]);
+        const R ir = R(1) / rho;
+        R ke = R(0);
         P[0] = rho;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            P[1 + c] = W[1 + c] * ir;
-            ke += W[1 + c] * P[1 + c];
+            P[1 + c] = R(W[1 + c]) * ir;
+            ke += R(W[1 + c]) * P[1 + c];
         }
-        P[D + 1] = (gam - 1.0) * (W[D + 1] - 0.5 * ke);
+        P[D + 1] = (gam - R(1)) * (R(W[D + 1]) - R(0.5) * ke);
     } else {
 #pragma unroll
-        for (int v = 0; v < M; ++v) P[v] = W[v];
+        for (int v = 0; v < M; ++v) P[v] = R(W[v]);
     }
 }
 
 // Numerical flux along direction k across the face between stencil cells 1
 // and 2 of a 4-cell stencil, from their reconstruction variables P(i, v).
-template <int EQ, int D, int M, class Acc>
-__device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, const Acc& P, double* F)
+template <int EQ, int D, int M, class R, class Acc>
+__device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, const Acc& P, R* F)
 {
+    const R h = R(0.5);
     if constexpr (EQ == 0) { // linear advection, centred flux
-        F[0] = g.phys[k] * (P(1, 0) + P(2, 0)) * 0.5;
+        F[0] = R(g.phys[k]) * (P(1, 0) + P(2, 0)) * h;
     } else if constexpr (EQ == 3) { // two-point diffusive flux
-        F[0] = -g.phys[0] * (P(2, 0) - P(1, 0)) / dxf;
+        F[0] = -R(g.phys[0]) * (P(2, 0) - P(1, 0)) / R(dxf);
     } else if constexpr (EQ == 1) { // Burgers: MUSCL-minmod + Godunov
-        const double u0 = P(0, 0), u1 = P(1, 0), u2 = P(2, 0), u3 = P(3, 0);
-        const double uL = u1 + 0.5 * minmod(u1 - u0, u2 - u1);
-        const double uR = u2 - 0.5 * minmod(u2 - u1, u3 - u2);
-        const double fL = 0.5 * uL * uL, fR = 0.5 * uR * uR;
-        if (uL <= uR) F[0] = uL > 0.0 ? fL : (uR < 0.0 ? fR : 0.0);
+        const R u0 = P(0, 0), u1 = P(1, 0), u2 = P(2, 0), u3 = P(3, 0);
+        const R uL = u1 + h * minmod(u1 - u0, u2 - u1);
+        const R uR = u2 - h * minmod(u2 - u1, u3 - u2);
+        const R fL = h * uL * uL, fR = h * uR * uR;
+        if (uL <= uR) F[0] = uL > R(0) ? fL : (uR < R(0) ? fR : R(0));
         else F[0] = fmax(fL, fR);
     } else { // Euler: MUSCL-minmod on (rho, u_1..u_d, p) + HLL
-        const double gam = g.phys[0];
-        double PL[M], PR[M];
+        const R gam = R(g.phys[0]);
+        R PL[M], PR[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-            const double a0 = P(0, v), a1 = P(1, v), a2 = P(2, v), a3 = P(3, v);
-            PL[v] = a1 + 0.5 * minmod(a1 - a0, a2 - a1);
-            PR[v] = a2 - 0.5 * minmod(a2 - a1, a3 - a2);
+            const R a0 = P(0, v), a1 = P(1, v), a2 = P(2, v), a3 = P(3, v);
+            PL[v] = a1 + h * minmod(a1 - a0, a2 - a1);
+            PR[v] = a2 - h * minmod(a2 - a1, a3 - a2);
         }
-        double UL[M], UR[M], FL[M], FR[M];
-        double keL = 0.0, keR = 0.0;
+        R UL[M], UR[M], FL[M], FR[M];
+        R keL = R(0), keR = R(0);
         UL[0] = PL[0];
         UR[0] = PR[0];
 #pragma unroll
@@ -359,10 +366,10 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
             keL += PL[1 + c] * PL[1 + c];
             keR += PR[1 + c] * PR[1 + c];
         }
-        const double igm = 1.0 / (gam - 1.0);
-        UL[D + 1] = PL[D + 1] * igm + 0.5 * PL[0] * keL;
-        UR[D + 1] = PR[D + 1] * igm + 0.5 * PR[0] * keR;
-        const double unL = PL[1 + k], unR = PR[1 + k];
+        const R igm = R(1) / (gam - R(1));
+        UL[D + 1] = PL[D + 1] * igm + h * PL[0] * keL;
+        UR[D + 1] = PR[D + 1] * igm + h * PR[0] * keR;
+        const R unL = PL[1 + k], unR = PR[1 + k];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
             FL[v] = UL[v] * unL;
@@ -372,18 +379,18 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
         FR[1 + k] += PR[D + 1];
         FL[D + 1] += PL[D + 1] * unL;
         FR[D + 1] += PR[D + 1] * unR;
-        const double cL = sqrt(gam * PL[D + 1] / PL[0]);
-        const double cR = sqrt(gam * PR[D + 1] / PR[0]);
-        const double sL = fmin(unL - cL, unR - cR);
-        const double sR = fmax(unL + cL, unR + cR);
-        if (sL >= 0.0) {
+        const R cL = sqrt(gam * PL[D + 1] / PL[0]);
+        const R cR = sqrt(gam * PR[D + 1] / PR[0]);
+        const R sL = fmin(unL - cL, unR - cR);
+        const R sR = fmax(unL + cL, unR + cR);
+        if (sL >= R(0)) {
 #pragma unroll
             for (int v = 0; v < M; ++v) F[v] = FL[v];
-        } else if (sR <= 0.0) {
+        } else if (sR <= R(0)) {
 #pragma unroll
             for (int v = 0; v < M; ++v) F[v] = FR[v];
         } else {
-            const double ids = 1.0 / (sR - sL);
+            const R ids = R(1) / (sR - sL);
 #pragma unroll
             for (int v = 0; v < M; ++v) F[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) * ids;
         }
@@ -391,13 +398,13 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
 }
 
 // numerical flux from the conservative values of the 4 stencil cells
-template <int EQ, int D, int M>
-__device__ __forceinline__ void num_flux(const Grid& g, int k, double dxf, const double (&W)[4][M], double* F)
+template <int EQ, int D, int M, class R>
+__device__ __forceinline__ void num_flux(const Grid& g, int k, double dxf, const double (&W)[4][M], R* F)
 {
-    double P[4][M];
+    R P[4][M];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) recon_vars<EQ, D, M>(g, W[i], P[i]);
-    flux_recon<EQ, D, M>(g, k, dxf, [&](int i, int v) { return P[i][v]; }, F);
+    for (int i = 0; i < 4; ++i) recon_vars<EQ, D, M, R>(g, W[i], P[i]);
+    flux_recon<EQ, D, M, R>(g, k, dxf, [&](int i, int v) { return P[i][v]; }, F);
 }
 
 template <int EQ, int M>

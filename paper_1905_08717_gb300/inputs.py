@@ -33,6 +33,9 @@ ADAPT_NEVER = 0
 ADAPT_MACRO = 1
 ADAPT_EVERY = 2
 
+PREC_FP64 = 0
+PREC_MIXED = 1   # FP32 face fluxes; state, registers and adaptation FP64
+
 
 @dataclass
 class Problem:
@@ -206,6 +209,43 @@ def euler_1d_sod(L: int = 8, eps: float = 1e-3, min_level: int = 2,
                 eps=eps, eps_mode=0, rk_order=rk_order, time_mode=time_mode,
                 cfl=0.5, bc=(BC_NEUMANN,) * 3, phys=ph, t_end=t_end,
                 name=f"euler1d_sod_L{L}")
+    return p, q
+
+
+def euler_3d_blast(L: int = 8, eps: float = 1e-3, min_level: int = 3,
+                   rk_order: int = 3, time_mode: int = TIME_LT,
+                   precision: int = 1, gamma: float = 1.4, r0: float = 0.1,
+                   p_in: float = 10.0, t_end: float = 0.1) -> tuple[Problem, np.ndarray]:
+    """3D Euler blast on [0,1]^3, homogeneous Neumann: rho = 1, u = 0, p = 1,
+    p = p_in inside the ball of radius r0 about the centre.  Cell averages of
+    p are exact away from the sphere; cells the sphere cuts use the fraction
+    of 4x4x4 midpoint sub-samples inside it."""
+    n = 1 << L
+    h = 1.0 / n
+    c = (np.arange(n) + 0.5) * h
+    d2 = ((c[None, None, :] - 0.5) ** 2 + (c[None, :, None] - 0.5) ** 2
+          + (c[:, None, None] - 0.5) ** 2)
+    half_diag = 0.5 * math.sqrt(3.0) * h
+    r = np.sqrt(d2)
+    frac = (r + half_diag <= r0).astype(np.float64)
+    cut = np.argwhere((r - half_diag < r0) & (r + half_diag > r0))
+    if len(cut):
+        o = (np.arange(4) + 0.5) / 4 - 0.5
+        OZ, OY, OX = (a.ravel()[None, :] for a in np.meshgrid(o, o, o, indexing="ij"))
+        z, y, x = cut[:, 0:1], cut[:, 1:2], cut[:, 2:3]
+        px = c[x] + OX * h - 0.5
+        py = c[y] + OY * h - 0.5
+        pz = c[z] + OZ * h - 0.5
+        frac[cut[:, 0], cut[:, 1], cut[:, 2]] = np.mean(px * px + py * py + pz * pz < r0 * r0, axis=1)
+    pr = 1.0 + (p_in - 1.0) * frac
+    q = np.zeros((5, n, n, n))
+    q[0] = 1.0
+    q[4] = pr / (gamma - 1.0)
+    ph = (gamma,) + (0.0,) * 7
+    p = Problem(dim=3, equation=EQ_EULER, max_level=L, min_level=min_level,
+                eps=eps, eps_mode=0, rk_order=rk_order, time_mode=time_mode,
+                precision=precision, cfl=0.5, bc=(BC_NEUMANN,) * 3, phys=ph,
+                t_end=t_end, name=f"euler3d_blast_L{L}")
     return p, q
 
 

@@ -1,0 +1,121 @@
+"""Mixed-precision mode (FP32 face fluxes, FP64 state / registers / adaptation)
+against the FP64 oracle.
+
+The mixed path cannot match the oracle to 1e-12: every face flux carries an
+FP32 rounding error.  The bar is the bound derived for it.  A flux evaluation of
+the MUSCL + HLL chain (about 60 dependent operations, cancellations included)
+is taken to lose at most C = 64 units of FP32 rounding, u32 = 2^-24.  Through
+an update dt_l / dx_l (F_{-} - F_{+}) with Courant number sigma, that gives a
+relative state error of at most 2 C u32 sigma per stage, and at most
+3 x 2 C u32 sigma per RK3 step.  Over n fine iterations, the error of the
+uniform reconstruction, in L1 relative to the oracle's L1 norm, is therefore
+bounded by
+
+    tol = n * 6 * C * u32 * sigma
+
+(linear accumulation, no cancellation assumed).  Thresholding decisions near
+eps can flip between the two runs.  A flipped node changes its cells by a
+detail of order eps * s_v, where s_v is the variable's scale, so flips add
+eps * (flipped fraction) to the bound.  The leaf-count check below limits that
+fraction, and the tests add eps * 1e-2.
+
+The tests also check that the mixed result differs from the GPU's own FP64
+result by more than FP64 round-off, so that the FP32 path really ran, and that
+it conserves mass to FP64 round-off, because every face flux enters both sides
+of the face and the registers are FP64."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_08717_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+C_FLUX = 64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_08717_gb300 import build
+    build.build()
+
+
+def _solver(p, q):
+    import paper_1905_08717_gb300 as pkg
+    return pkg.Solver(p, q)
+
+
+def _rel_l1(a, b):
+    """per-variable L1 difference relative to the L1 norm of b"""
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.abs(a - b).sum(axis=1) / np.maximum(np.abs(b).sum(axis=1), 1e-300)
+
+
+def _check(p, q, t):
+    """run mixed GPU, FP64 GPU and the FP64 oracle to t; return the errors"""
+    pm = p.replace(precision=I.PREC_MIXED)
+    p64 = p.replace(precision=I.PREC_FP64)
+    gm, g64, ref = _solver(pm, q), _solver(p64, q), oracle.Oracle(p64, q)
+    gm.step(t)
+    g64.step(t)
+    ref.step(t)
+    sm, so = gm.stats(), ref.stats()
+    n = so["iters"]
+    assert sm["iters"] == n
+    tol = n * 6 * C_FLUX * U32 * p.cfl + p.eps * 1e-2
+    uo = ref.uniform()
+    e_mixed = _rel_l1(gm.uniform(), uo)
+    e_fp64 = _rel_l1(g64.uniform(), uo)
+    assert e_fp64.max() <= 1e-12, f"FP64 GPU path off the oracle: {e_fp64}"
+    assert e_mixed.max() <= tol, f"mixed L1 error {e_mixed} above the bound {tol:.3e}"
+    assert e_mixed.max() > 1e-12, "mixed result equals the FP64 one: FP32 flux path not taken"
+    # thresholding flips stay rare
+    assert abs(sm["leaves"] - so["leaves"]) <= 0.02 * so["leaves"] + 8
+    return e_mixed, tol
+
+
+def test_mixed_burgers_1d():
+    p, q = I.burgers_1d(L=10, eps=1e-3)
+    _check(p, q, 0.3)
+
+
+def test_mixed_euler_2d_quadrants():
+    p, q = I.euler_2d_quadrants(L=7, eps=1e-3, seed=0)
+    _check(p, q, 0.1)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_mixed_euler_2d_quadrants_random_states(seed):
+    p, q = I.euler_2d_quadrants(L=6, eps=1e-3, seed=seed)
+    _check(p, q, 0.1)
+
+
+def test_mixed_rd_2d_rk2():
+    p, q = I.rd_bumps_2d(L=7, eps=1e-3, seed=1)
+    _check(p, q, 0.05)
+
+
+def test_mixed_euler_3d_blast():
+    p, q = I.euler_3d_blast(L=5, eps=1e-2, min_level=2)
+    _check(p, q, 0.02)
+
+
+def test_mixed_conserves_mass():
+    """periodic 2D Euler: flux registers keep the FP32-flux run conservative"""
+    p, q = I.euler_2d_quadrants(L=7, eps=1e-3, seed=0)
+    p = p.replace(bc=(I.BC_PERIODIC,) * 3, precision=I.PREC_MIXED)
+    g = _solver(p, q)
+    m0 = np.array(g.stats()["mass"])
+    g.step(0.05)
+    m1 = np.array(g.stats()["mass"])
+    scale = np.abs(q.reshape(q.shape[0], -1)).max(axis=1)
+    assert np.all(np.abs(m1 - m0)[: len(scale)] <= 1e-12 * scale)
+
+
+def test_mixed_gts_mode():
+    p, q = I.euler_2d_quadrants(L=6, eps=1e-3, seed=0, time_mode=I.TIME_GTS)
+    _check(p, q, 0.1)
