@@ -26,6 +26,7 @@ struct mr_solver {
     double t = 0.0, dt = 0.0;
     long long iters = 0, macros = 0, pos = 0, stage_launches = 0;
     bool reg = false;
+    bool launch_failed = false; // a stage launch could not be configured
     std::string err;
     // stage-kernel timing (mr_profile)
     bool prof = false;
@@ -133,15 +134,24 @@ void stage(mr_solver* h, int lo, int hi, int s, int lmin, double dt)
         launched = launch_stage(g, h->stream, lo, hi, s, lmin, dt, b, reg);
         cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
         ++h->ev_used;
-        h->prof_launches += launched;
+        h->prof_launches += launched > 0 ? launched : 0;
     } else {
         launched = launch_stage(g, h->stream, lo, hi, s, lmin, dt, b, reg);
+    }
+    if (launched < 0) {
+        h->launch_failed = true;
+        return;
     }
     h->stage_launches += launched;
 }
 
 mr_status sync_check(mr_solver* h)
 {
+    if (h->launch_failed) {
+        h->launch_failed = false;
+        h->err = "stage kernel could not be configured (shared memory or occupancy query failed)";
+        return MR_E_CUDA;
+    }
     MR_CK(cudaGetLastError());
     MR_CK(cudaStreamSynchronize(h->stream));
     int e = 0;
@@ -338,9 +348,13 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     long long off = 0, toff = 0;
     for (int l = g.lb; l <= g.L; ++l) {
         g.toff[l] = toff;
-        g.ntx[l] = g.d == 1 ? (int)((1LL << l) + kTile1X - 1) / kTile1X : (int)((1LL << l) + kTile2X - 1) / kTile2X;
-        g.nty[l] = g.d == 2 ? (int)((1LL << l) + kTile2Y - 1) / kTile2Y : 1;
-        toff += (long long)g.ntx[l] * g.nty[l];
+        const long long nl = 1LL << l;
+        const int tx = g.d == 1 ? kTile1X : (g.d == 2 ? kTile2X : kTile3X);
+        const int ty = g.d == 2 ? kTile2Y : kTile3Y;
+        g.ntx[l] = (int)((nl + tx - 1) / tx);
+        g.nty[l] = g.d >= 2 ? (int)((nl + ty - 1) / ty) : 1;
+        g.ntz[l] = g.d == 3 ? (int)((nl + kTile3Z - 1) / kTile3Z) : 1;
+        toff += (long long)g.ntx[l] * g.nty[l] * g.ntz[l];
         g.off[l] = off;
         g.N[l] = 1LL << (g.d * l);
         g.n[l] = 1 << l;

@@ -25,9 +25,10 @@ namespace mrlt {
 constexpr int LMAX = 16;
 constexpr int MMAX = 5;
 constexpr int NTHREADS = 128;
-// tiles of the tiled stage kernel (d = 1: 64 cells; d = 2: 16 x 16 cells)
+// tiles of the tiled stage kernel (d = 1: 64 cells; d = 2: 16 x 8; d = 3: 8 x 4 x 4)
 constexpr int kTile1X = 64;
-constexpr int kTile2X = 16, kTile2Y = 16;
+constexpr int kTile2X = 16, kTile2Y = 8;
+constexpr int kTile3X = 8, kTile3Y = 4, kTile3Z = 4;
 
 enum Field { F_Q0 = 0, F_Q1, F_Q2, F_QE, F_XH, F_NH, F_N1, F_N3, NFIELD };
 enum Kind { K_WALL = 0, K_LEAF = 1, K_FINER = 2, K_COARSER = 3 };
@@ -43,7 +44,7 @@ struct Grid {
     int* leaves;
     int* inner;
     int* counts;                    // [0..LMAX] leaves, [LMAX+1..] internal nodes, [2(LMAX+1)..] active tiles
-    uint8_t* tflag;                 // per-level tile flags (tile holds a leaf), d <= 2
+    uint8_t* tflag;                 // per-level tile flags (tile holds a leaf)
     int* tlist;                     // per-level lists of active tiles, ascending
     double* scale;                  // [MMAX] detail normalisation s_v
     unsigned long long* scale_bits; // [MMAX] running max |q_v| (bit pattern)
@@ -58,7 +59,7 @@ struct Grid {
     double dx[LMAX + 1][3];
     double rdx[LMAX + 1][3];        // 1 / dx
     long long toff[LMAX + 1];       // tile offset of each level in tflag / tlist
-    int ntx[LMAX + 1], nty[LMAX + 1]; // tiles per direction
+    int ntx[LMAX + 1], nty[LMAX + 1], ntz[LMAX + 1]; // tiles per direction
     int d, m, nf, L, lb, eq, rk, gts;
     int bc[3];
     double phys[8];
@@ -395,16 +396,6 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
             for (int v = 0; v < M; ++v) F[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) * ids;
         }
     }
-}
-
-// numerical flux from the conservative values of the 4 stencil cells
-template <int EQ, int D, int M, class R>
-__device__ __forceinline__ void num_flux(const Grid& g, int k, double dxf, const double (&W)[4][M], R* F)
-{
-    R P[4][M];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) recon_vars<EQ, D, M, R>(g, W[i], P[i]);
-    flux_recon<EQ, D, M, R>(g, k, dxf, [&](int i, int v) { return P[i][v]; }, F);
 }
 
 template <int EQ, int M>

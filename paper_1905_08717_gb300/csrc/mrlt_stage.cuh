@@ -1,82 +1,15 @@
 // mrlt_stage.cuh -- the stage kernels of the MR/MRLT time evolution: face
 // fluxes from the exposures of Secs. 4.1-4.3, the compact RK update of Sec. 3
 // and the flux-register epilogue.
-//  - k_stage_tile (d = 1, 2): one CTA per tile of one level; the halo is
-//    staged in shared memory and every face flux is computed once.
-//  - k_stage (d = 3): one thread per leaf.
-// Both are instantiated for R = double and, for the mixed-precision mode, for
-// R = float: reconstruction and numerical flux in R; the stored state, the
-// right-hand side, the RK update and the flux registers stay in double.
+// k_stage_tile (d = 1, 2, 3) works on one tile of one level per CTA: the
+// halo is staged in shared memory and every face flux is computed once.  It is
+// instantiated for R = double and, for the mixed-precision mode, R = float:
+// reconstruction and numerical flux in R; the stored state, the right-hand
+// side, the RK update and the flux registers stay in double.
 #pragma once
 #include "mrlt_impl.cuh"
 
 namespace mrlt {
-
-// Face flux of the leaf at c (level u) in direction k, side -1/+1, oriented
-// along +x_k (Sec. 2 flux scenarios).  Returns the face kind.
-template <int EQ, int D, int M, class R>
-__device__ __forceinline__ int face_flux(const Grid& g, const Ctx& x, int u, const int c[3], int k,
-                                         int side, double* F)
-{
-    int kind, q;
-    bool sub = false;
-    if (!in_box(g, u, k, c[k] + side, &q)) {
-        kind = K_WALL;
-    } else {
-        int nb[3] = {c[0], c[1], c[2]};
-        nb[k] = q;
-        const int s = status(g, u, cell_id(g, u, nb[0], nb[1], nb[2]));
-        if (s == 2 && u < g.L) {
-            sub = true;
-            kind = K_FINER;
-        } else {
-            kind = s == 1 ? K_LEAF : K_COARSER;
-        }
-    }
-    double W[4][M];
-    if (!sub) {
-        int p[3] = {c[0], c[1], c[2]};
-        const int first = side > 0 ? c[k] - 1 : c[k] - 2;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            p[k] = first + i;
-            value_at<D, M>(g, x, u, p, W[i]);
-        }
-        R Fr[M];
-        num_flux<EQ, D, M, R>(g, k, g.dx[u][k], W, Fr);
-#pragma unroll
-        for (int v = 0; v < M; ++v) F[v] = double(Fr[v]);
-        return kind;
-    }
-    // internal neighbour: mean of the 2^{d-1} sub-face fluxes on level u+1
-    constexpr int NT = 1 << (D - 1);
-    double acc[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) acc[v] = 0.0;
-#pragma unroll 1
-    for (int t = 0; t < NT; ++t) {
-        int p[3] = {0, 0, 0}, bit = 0;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            if (j == k) continue;
-            p[j] = 2 * c[j] + ((t >> bit) & 1);
-            ++bit;
-        }
-        const int first = side > 0 ? 2 * c[k] : 2 * c[k] - 2;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            p[k] = first + i;
-            value_at<D, M>(g, x, u + 1, p, W[i]);
-        }
-        R Fs[M];
-        num_flux<EQ, D, M, R>(g, k, g.dx[u + 1][k], W, Fs);
-#pragma unroll
-        for (int v = 0; v < M; ++v) acc[v] += double(Fs[v]);
-    }
-#pragma unroll
-    for (int v = 0; v < M; ++v) F[v] = acc[v] * (1.0 / NT);
-    return kind;
-}
 
 // Compact RK update of one leaf from its right-hand side f (Sec. 3):
 //   s = 1: q*  = q^n + dt_l f
@@ -116,55 +49,28 @@ __device__ __forceinline__ void reg_add(const Grid& g, int u, long long id, int 
     for (int v = 0; v < M; ++v) R[(fi * M + v) * N] += bw * F[v];
 }
 
-// One compact RK stage of every leaf of level u, one thread per leaf (d = 3).
-template <int EQ, int D, class R>
-__global__ void __launch_bounds__(NTHREADS) k_stage(Grid g, int u, int s, int lmin, double dtl,
-                                                    double bw, int reg)
-{
-    constexpr int M = EQ == 2 ? D + 2 : 1;
-    const int cnt = g.counts[u];
-    const int* list = g.leaves + g.off[u];
-    const long long N = g.N[u];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (s == 1) atomicAdd(g.updates, (unsigned long long)cnt);
-        atomicAdd(&g.work[u * 4 + s], (unsigned long long)cnt);
-    }
-    const Ctx x{u, s, lmin};
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
-        const long long id = list[t];
-        if (id < 0 || id >= N) {
-            atomicOr(g.err, ERR_INDEX);
-            continue;
-        }
-        int c[3];
-        cell_xyz(g, u, id, c);
-        double self[M], f[M];
-        expose<M>(g, x, u, id, 1, self);
-        source<EQ, M>(g, self, f);
-#pragma unroll 1
-        for (int k = 0; k < D; ++k) {
-            double Fm[M], Fp[M];
-            const int km = face_flux<EQ, D, M, R>(g, x, u, c, k, -1, Fm);
-            const int kp = face_flux<EQ, D, M, R>(g, x, u, c, k, +1, Fp);
-            const double idx = g.rdx[u][k];
-#pragma unroll
-            for (int v = 0; v < M; ++v) f[v] += (Fm[v] - Fp[v]) * idx;
-            if (reg) {
-                reg_add<M>(g, u, id, 2 * k, km, bw, Fm);
-                reg_add<M>(g, u, id, 2 * k + 1, kp, bw, Fp);
-            }
-        }
-        rk_update<M>(g, u, id, s, dtl, f);
-    }
-}
-
-// Tile shapes of the tiled stage kernel: a CTA owns TX x TY cells of one level
-// (the same shapes index the per-level active-tile lists).
+// Tile shapes of the tiled stage kernel: a CTA owns TX x TY x TZ cells of one
+// level (the same shapes index the per-level active-tile lists).
 template <int D> struct Tile;
-template <> struct Tile<1> { static constexpr int TX = kTile1X, TY = 1; };
-template <> struct Tile<2> { static constexpr int TX = kTile2X, TY = kTile2Y; };
-// resident CTAs of a persistent stage launch (152 SMs x 3)
-constexpr long long kStageCtas = 456;
+template <> struct Tile<1> { static constexpr int TX = kTile1X, TY = 1, TZ = 1; };
+template <> struct Tile<2> { static constexpr int TX = kTile2X, TY = kTile2Y, TZ = 1; };
+template <> struct Tile<3> { static constexpr int TX = kTile3X, TY = kTile3Y, TZ = kTile3Z; };
+
+// Block (tile + 2-cell ring) and face counts of one tile; the three large
+// shared arrays (conservative values, reconstruction variables, face fluxes)
+// live in dynamic shared memory, SMEM bytes.
+template <int EQ, int D, class R>
+struct TileShape {
+    static constexpr int M = EQ == 2 ? D + 2 : 1;
+    static constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, NT = TX * TY * TZ, H = 2;
+    static constexpr int BX = TX + 2 * H, BY = D > 1 ? TY + 2 * H : 1, BZ = D > 2 ? TZ + 2 * H : 1;
+    static constexpr int NB = BX * BY * BZ;
+    static constexpr int NFX = (TX + 1) * TY * TZ;
+    static constexpr int NFY = D > 1 ? TX * (TY + 1) * TZ : 0;
+    static constexpr int NFZ = D > 2 ? TX * TY * (TZ + 1) : 0;
+    static constexpr int NF = NFX + NFY + NFZ;
+    static constexpr size_t SMEM = sizeof(double) * M * NB + sizeof(R) * M * NB + sizeof(R) * M * NF;
+};
 
 // Append, in thread order, the items for which `take` holds to a shared list
 // (warp ballots and a block-wide prefix); every thread of the block calls it
@@ -188,7 +94,7 @@ __device__ __forceinline__ int block_append(bool take, int item, short* list, in
     return len + total;
 }
 
-// Tiled stage (d = 1, 2).  The CTA
+// Tiled stage (d = 1, 2, 3).  The CTA
 //  1. reads the status of its tile and a 2-cell ring; tiles without leaves exit;
 //  2. lists the cells some leaf of the tile reads -- its radius-2 cross stencil,
 //     plus the 3^d block of a leaf facing an internal node -- and stages their
@@ -197,24 +103,28 @@ __device__ __forceinline__ int block_append(bool take, int item, short* list, in
 //  3. lists the faces touching a tile leaf and computes each once: plain faces
 //     on level u from the shared cells; faces of a leaf against an internal node
 //     as the mean of 2^{d-1} sub-face fluxes on level u+1 (Sec. 2), one thread
-//     per sub-face, the leaf's virtual children predicted (Eq. 4) from its
-//     shared 3^d block and the finer side read from level u+1;
+//     per sub-face (the 2^{d-1} threads of a face are adjacent lanes), the
+//     leaf's virtual children predicted (Eq. 4) from its shared 3^d block and
+//     the finer side read from level u+1;
 //  4. applies the compact RK update and the register epilogue to its leaves.
 // Work lists keep every warp on one kind of work.
 template <int EQ, int D, class R>
-__global__ void __launch_bounds__(Tile<D>::TX * Tile<D>::TY)
+__global__ void __launch_bounds__(Tile<D>::TX * Tile<D>::TY * Tile<D>::TZ)
 k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, int reg)
 {
-    constexpr int M = EQ == 2 ? D + 2 : 1;
-    constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, NT = TX * TY, H = 2;
-    constexpr int BX = TX + 2 * H, BY = D > 1 ? TY + 2 * H : 1, NB = BX * BY;
-    constexpr int NFX = (TX + 1) * TY, NFY = D > 1 ? TX * (TY + 1) : 0, NF = NFX + NFY;
+    using S = TileShape<EQ, D, R>;
+    constexpr int M = S::M, TX = S::TX, TY = S::TY, TZ = S::TZ, NT = S::NT, H = S::H;
+    constexpr int BX = S::BX, BY = S::BY, NB = S::NB;
+    constexpr int NFX = S::NFX, NFY = S::NFY, NF = S::NF;
     constexpr int NTS = 1 << (D - 1); // sub-faces per face
     constexpr int NL = NB > NF ? NB : NF;
     constexpr int OUT = 3;            // status code of a cell past a wall
-    __shared__ double sW[M][NB];
-    __shared__ R sP[M][NB];
-    __shared__ R sF[M][NF];           // x faces [0, NFX), y faces [NFX, NF)
+    constexpr int SY = BX, SZ = BX * BY; // block strides in y and z
+    extern __shared__ __align__(16) unsigned char smem[];
+    double (*sW)[NB] = reinterpret_cast<double (*)[NB]>(smem);
+    R (*sP)[NB] = reinterpret_cast<R (*)[NB]>(smem + sizeof(double) * M * NB);
+    // x faces [0, NFX), y faces [NFX, NFX + NFY), z faces [NFX + NFY, NF)
+    R (*sF)[NF] = reinterpret_cast<R (*)[NF]>(smem + (sizeof(double) + sizeof(R)) * M * NB);
     __shared__ uint8_t sSt[NB];
     __shared__ short sList[NL];
     __shared__ int sWarp[NT / 32];
@@ -240,70 +150,86 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
     const double dtl = g.gts ? dt : ldexp(dt, g.L - u); // Eq. 13 step of level u
     const double bw = dtl * bstage; // register weight dt_l b_s
     const int n = g.n[u];
-    const int ntx = (n + TX - 1) / TX;
+    const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
     const int ox = (tile % ntx) * TX;
-    const int oy = D > 1 ? (tile / ntx) * TY : 0;
+    const int oy = D > 1 ? ((tile / ntx) % nty) * TY : 0;
+    const int oz = D > 2 ? (tile / (ntx * nty)) * TZ : 0;
     const int tid = threadIdx.x;
     const Ctx x{u, s, lmin};
     const bool finer = u < g.L; // internal nodes of level u have children
 
-    // is block cell (bx, by) a leaf of this tile?
-    auto tile_leaf = [&](int bx, int by) -> bool {
+    // is block cell (bx, by, bz) a leaf of this tile?
+    auto tile_leaf = [&](int bx, int by, int bz) -> bool {
         if (bx < H || bx >= H + TX || ox + bx - H >= n) return false;
         if (D > 1 && (by < H || by >= H + TY || oy + by - H >= n)) return false;
-        return sSt[by * BX + bx] == 1;
+        if (D > 2 && (bz < H || bz >= H + TZ || oz + bz - H >= n)) return false;
+        return sSt[bz * SZ + by * SY + bx] == 1;
     };
     // a tile leaf with an internal node across one of its faces
-    auto leaf_li = [&](int bx, int by) -> bool {
-        if (!finer || !tile_leaf(bx, by)) return false;
-        const int b = by * BX + bx;
+    auto leaf_li = [&](int bx, int by, int bz) -> bool {
+        if (!finer || !tile_leaf(bx, by, bz)) return false;
+        const int b = bz * SZ + by * SY + bx;
         bool li = sSt[b - 1] == 2 || sSt[b + 1] == 2;
-        if (D > 1) li = li || sSt[b - BX] == 2 || sSt[b + BX] == 2;
+        if (D > 1) li = li || sSt[b - SY] == 2 || sSt[b + SY] == 2;
+        if (D > 2) li = li || sSt[b - SZ] == 2 || sSt[b + SZ] == 2;
         return li;
     };
     auto needed = [&](int b) -> bool {
-        const int bx = b % BX, by = b / BX;
+        const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
         bool need = false;
 #pragma unroll
         for (int d = -2; d <= 2; ++d) {
-            need = need || tile_leaf(bx + d, by);
-            if (D > 1) need = need || tile_leaf(bx, by + d);
+            need = need || tile_leaf(bx + d, by, bz);
+            if (D > 1) need = need || tile_leaf(bx, by + d, bz);
+            if (D > 2) need = need || tile_leaf(bx, by, bz + d);
         }
 #pragma unroll
-        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
+        for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz)
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) need = need || leaf_li(bx + dx, by + dy);
+            for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) need = need || leaf_li(bx + dx, by + dy, bz + dz);
         return need;
     };
     // geometry of face f: the cells on its two sides and the direction
     auto face = [&](int f, int& k, int& lo, int& hi, bool& leafLo, bool& leafHi) {
         if (f < NFX) {
-            const int i = f % (TX + 1), j = f / (TX + 1);
-            const int by = D > 1 ? H + j : 0;
+            const int i = f % (TX + 1), r = f / (TX + 1), j = r % TY, kz = r / TY;
+            const int by = D > 1 ? H + j : 0, bz = D > 2 ? H + kz : 0;
             k = 0;
-            lo = by * BX + H + i - 1;
+            lo = bz * SZ + by * SY + H + i - 1;
             hi = lo + 1;
-            leafLo = tile_leaf(H + i - 1, by);
-            leafHi = tile_leaf(H + i, by);
-        } else {
-            const int ff = f - NFX, i = ff % TX, j = ff / TX;
+            leafLo = tile_leaf(H + i - 1, by, bz);
+            leafHi = tile_leaf(H + i, by, bz);
+        } else if (D < 3 || f < NFX + NFY) {
+            const int ff = f - NFX, i = ff % TX, r = ff / TX, j = r % (TY + 1), kz = r / (TY + 1);
+            const int bz = D > 2 ? H + kz : 0;
             k = 1;
-            lo = (H + j - 1) * BX + H + i;
-            hi = lo + BX;
-            leafLo = tile_leaf(H + i, H + j - 1);
-            leafHi = tile_leaf(H + i, H + j);
+            lo = bz * SZ + (H + j - 1) * SY + H + i;
+            hi = lo + SY;
+            leafLo = tile_leaf(H + i, H + j - 1, bz);
+            leafHi = tile_leaf(H + i, H + j, bz);
+        } else {
+            const int ff = f - NFX - NFY, i = ff % TX, r = ff / TX, j = r % TY, kz = r / TY;
+            k = 2;
+            lo = (H + kz - 1) * SZ + (H + j) * SY + H + i;
+            hi = lo + SZ;
+            leafLo = tile_leaf(H + i, H + j, H + kz - 1);
+            leafHi = tile_leaf(H + i, H + j, H + kz);
         }
     };
 
     // 1. status of the tile and its ring
     for (int b = tid; b < NB; b += NT) {
-        const int bx = b % BX, by = b / BX;
-        int qx, qy = 0;
-        const bool inb = in_box(g, u, 0, ox + bx - H, &qx) && (D < 2 || in_box(g, u, 1, oy + by - H, &qy));
-        sSt[b] = inb ? status(g, u, cell_id(g, u, qx, qy, 0)) : OUT;
+        const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
+        int qx, qy = 0, qz = 0;
+        const bool inb = in_box(g, u, 0, ox + bx - H, &qx) && (D < 2 || in_box(g, u, 1, oy + by - H, &qy)) &&
+                         (D < 3 || in_box(g, u, 2, oz + bz - H, &qz));
+        sSt[b] = inb ? status(g, u, cell_id(g, u, qx, qy, qz)) : OUT;
     }
     __syncthreads();
-    const int nleaf = __syncthreads_count(tile_leaf(H + tid % TX, D > 1 ? H + tid / TX : 0));
+    const int nleaf = __syncthreads_count(
+        tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0));
     if (nleaf == 0) continue; // uniform across the CTA
     if (tid == 0) {
         if (s == 1) atomicAdd(g.updates, (unsigned long long)nleaf);
@@ -323,16 +249,17 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
     }
     for (int t = tid; t < ncell; t += NT) {
         const int b = sList[t];
-        const int bx = b % BX, by = b / BX;
+        const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
         double W[M];
         R P[M];
         if (t < nst) {
-            int qx, qy = 0;
+            int qx, qy = 0, qz = 0;
             in_box(g, u, 0, ox + bx - H, &qx);
             if (D > 1) in_box(g, u, 1, oy + by - H, &qy);
-            expose<M>(g, x, u, cell_id(g, u, qx, qy, 0), sSt[b], W);
+            if (D > 2) in_box(g, u, 2, oz + bz - H, &qz);
+            expose<M>(g, x, u, cell_id(g, u, qx, qy, qz), sSt[b], W);
         } else {
-            const int p[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, 0};
+            const int p[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, D > 2 ? oz + bz - H : 0};
             value_at<D, M>(g, x, u, p, W);
         }
         recon_vars<EQ, D, M, R>(g, W, P);
@@ -363,7 +290,7 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
         int k, lo, hi;
         bool lL, lH;
         face(f, k, lo, hi, lL, lH);
-        const int stride = k == 0 ? 1 : BX;
+        const int stride = k == 0 ? 1 : (k == 1 ? SY : SZ);
         R F[M];
         flux_recon<EQ, D, M, R>(g, k, g.dx[u][k], [&](int c, int v) { return sP[v][lo + (c - 1) * stride]; }, F);
 #pragma unroll
@@ -399,46 +326,56 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
             face(f, k, lo, hi, lL, lH);
             const bool leafIsLo = lL && sSt[hi] == 2;
             const int bl = leafIsLo ? lo : hi, side = leafIsLo ? 1 : -1;
-            const int bx = bl % BX, by = bl / BX;
-            const int c0 = ox + bx - H, c1 = D > 1 ? oy + by - H : 0;
+            const int bx = bl % BX, by = (bl / BX) % BY, bz = bl / SZ;
+            const int c[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, D > 2 ? oz + bz - H : 0};
+            // tangential directions of the face, in increasing order; sub-face
+            // t takes child offset (t & 1) along the first, (t >> 1) along the second
+            const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
             R P4[4][M];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                // stencil cell i on level u+1: fine coordinate along k and along
-                // the face; the leaf's own children are virtual
-                const int fk = (k == 0 ? 2 * c0 : 2 * c1) + (side > 0 ? i : i - 2);
-                const int ft = (k == 0 ? 2 * c1 : 2 * c0) + t;
+                // stencil cell i on level u+1; the leaf's own children are virtual
+                int p[3] = {0, 0, 0};
+                p[k] = 2 * c[k] + (side > 0 ? i : i - 2);
+                if (D > 1) p[j1] = 2 * c[j1] + (t & 1);
+                if (D > 2) p[j2] = 2 * c[j2] + (t >> 1);
                 const bool own = side > 0 ? i < 2 : i >= 2;
                 double W[M];
                 if (own) {
-                    const int ax = k == 0 ? (fk & 1) : (ft & 1);
-                    const int ay = k == 0 ? (ft & 1) : (fk & 1);
+                    const int ax = p[0] & 1, ay = p[1] & 1, az = p[2] & 1;
 #pragma unroll
                     for (int v = 0; v < M; ++v) W[v] = 0.0;
 #pragma unroll
-                    for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
+                    for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz)
 #pragma unroll
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const double w = (D > 1 ? pw(ay, dy) : 1.0) * pw(ax, dx);
-                            const int bs = (by + dy) * BX + bx + dx;
+                        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
 #pragma unroll
-                            for (int v = 0; v < M; ++v) W[v] += w * sW[v][bs];
-                        }
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const double w = ((D > 2 ? pw(az, dz) : 1.0) * (D > 1 ? pw(ay, dy) : 1.0)) *
+                                                 pw(ax, dx);
+                                const int bs = bl + dz * SZ + dy * SY + dx;
+#pragma unroll
+                                for (int v = 0; v < M; ++v) W[v] += w * sW[v][bs];
+                            }
                 } else {
-                    int p[3] = {0, 0, 0};
-                    p[k] = fk;
-                    if (D > 1) p[1 - k] = ft;
                     value_at<D, M>(g, x, u + 1, p, W);
                 }
                 recon_vars<EQ, D, M, R>(g, W, P4[i]);
             }
-            flux_recon<EQ, D, M, R>(g, k, g.dx[u + 1][k], [&](int c, int v) { return P4[c][v]; }, F);
+            flux_recon<EQ, D, M, R>(g, k, g.dx[u + 1][k], [&](int cc, int v) { return P4[cc][v]; }, F);
         }
         if constexpr (NTS == 2) { // the two sub-faces of a face sit in lanes 2i, 2i+1
 #pragma unroll
             for (int v = 0; v < M; ++v) {
                 const R other = __shfl_xor_sync(0xffffffffu, F[v], 1);
                 if (act && t == 0) sF[v][f] = (F[v] + other) * R(0.5);
+            }
+        } else if constexpr (NTS == 4) { // lanes 4i .. 4i+3
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+                const R pair = F[v] + __shfl_xor_sync(0xffffffffu, F[v], 1);
+                const R quad = pair + __shfl_xor_sync(0xffffffffu, pair, 2);
+                if (act && t == 0) sF[v][f] = quad * R(0.25);
             }
         } else if (act) {
 #pragma unroll
@@ -449,19 +386,30 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
 
     // 4. compact RK update of the tile's leaves
     {
-        const int i = tid % TX, j = D > 1 ? tid / TX : 0;
-        const int bx = H + i, by = D > 1 ? H + j : 0, b = by * BX + bx;
-        if (tile_leaf(bx, by)) {
-        const long long id = cell_id(g, u, ox + i, oy + j, 0);
+        const int i = tid % TX, j = D > 1 ? (tid / TX) % TY : 0, kz = D > 2 ? tid / (TX * TY) : 0;
+        const int bx = H + i, by = D > 1 ? H + j : 0, bz = D > 2 ? H + kz : 0;
+        const int b = bz * SZ + by * SY + bx;
+        if (tile_leaf(bx, by, bz)) {
+        const long long id = cell_id(g, u, ox + i, oy + j, oz + kz);
         double self[M], f[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) self[v] = sW[v][b];
         source<EQ, M>(g, self, f);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            const int bm = k == 0 ? b - 1 : b - BX, bp = k == 0 ? b + 1 : b + BX;
-            const int fm = k == 0 ? j * (TX + 1) + i : NFX + j * TX + i;
-            const int fp = k == 0 ? fm + 1 : fm + TX;
+            const int stride = k == 0 ? 1 : (k == 1 ? SY : SZ);
+            const int bm = b - stride, bp = b + stride;
+            int fm, fp;
+            if (k == 0) {
+                fm = i + (TX + 1) * (j + TY * kz);
+                fp = fm + 1;
+            } else if (k == 1) {
+                fm = NFX + i + TX * (j + (TY + 1) * kz);
+                fp = fm + TX;
+            } else {
+                fm = NFX + NFY + i + TX * (j + TY * kz);
+                fp = fm + TX * TY;
+            }
             const int sm = sSt[bm], sp = sSt[bp];
             const int km = (sm == 2 && finer) ? K_FINER : (sm == 1 ? K_LEAF : (sm == OUT ? K_WALL : K_COARSER));
             const int kp = (sp == 2 && finer) ? K_FINER : (sp == 1 ? K_LEAF : (sp == OUT ? K_WALL : K_COARSER));
@@ -492,23 +440,34 @@ static inline int grid_for(const Grid& g, int l)
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
 }
 
+// One launch of the tiled stage kernel over the active tiles of levels lo..hi;
+// the persistent grid is the device's resident capacity for this instantiation
+// (occupancy API, once per device), capped by the tile count.
 template <int EQ, int D, class R>
 static int stage_dispatch(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt,
                           double b, int reg)
 {
-    if constexpr (D <= 2) {
-        long long total = 0;
-        for (int l = lo; l <= hi; ++l) total += (long long)g.ntx[l] * g.nty[l];
-        const long long grid = total < kStageCtas ? total : kStageCtas;
-        k_stage_tile<EQ, D, R><<<(unsigned)grid, Tile<D>::TX * Tile<D>::TY, 0, st>>>(g, lo, hi, s, lmin, dt, b, reg);
-        return 1;
-    } else {
-        for (int u = lo; u <= hi; ++u) {
-            const double dtl = g.gts ? dt : ldexp(dt, g.L - u);
-            k_stage<EQ, D, R><<<grid_for(g, u), NTHREADS, 0, st>>>(g, u, s, lmin, dtl, dtl * b, reg);
-        }
-        return hi - lo + 1;
+    using S = TileShape<EQ, D, R>;
+    constexpr int kMaxDev = 64;
+    static int resident[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return -1;
+    if (!resident[dev]) {
+        if (cudaFuncSetAttribute(k_stage_tile<EQ, D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)S::SMEM) != cudaSuccess)
+            return -1;
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_tile<EQ, D, R>, S::NT, S::SMEM) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+            return -1;
+        resident[dev] = per_sm * sms;
     }
+    long long total = 0;
+    for (int l = lo; l <= hi; ++l) total += (long long)g.ntx[l] * g.nty[l] * g.ntz[l];
+    const long long grid = total < resident[dev] ? total : resident[dev];
+    k_stage_tile<EQ, D, R><<<(unsigned)grid, S::NT, S::SMEM, st>>>(g, lo, hi, s, lmin, dt, b, reg);
+    return 1;
 }
 
 // stage launcher of one equation (all dimensions, both precisions); each is

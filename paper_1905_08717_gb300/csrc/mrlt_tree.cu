@@ -482,11 +482,12 @@ __global__ void k_cmp_scatter(Grid g, LevelBlocks lbk, const int* bc)
     const unsigned below = (1u << lane) - 1u;
     if (s == 1) g.leaves[g.off[l] + wl[warp] + __popc(bl & below)] = (int)i;
     if (s == 2) g.inner[g.off[l] + wi[warp] + __popc(bi & below)] = (int)i;
-    if (s == 1 && g.d <= 2) { // the leaf's tile is active
-        const int n = g.n[l];
-        const int tx = g.d == 1 ? kTile1X : kTile2X;
-        const long long x = i % n, y = g.d == 2 ? i / n : 0;
-        g.tflag[g.toff[l] + x / tx + (long long)g.ntx[l] * (y / kTile2Y)] = 1;
+    if (s == 1) { // the leaf's tile is active
+        const long long n = g.n[l];
+        const int tx = g.d == 1 ? kTile1X : (g.d == 2 ? kTile2X : kTile3X);
+        const int ty = g.d == 2 ? kTile2Y : kTile3Y;
+        const long long x = i % n, y = g.d >= 2 ? (i / n) % n : 0, z = g.d == 3 ? i / (n * n) : 0;
+        g.tflag[g.toff[l] + x / tx + (long long)g.ntx[l] * (y / ty + (long long)g.nty[l] * (z / kTile3Z))] = 1;
     }
 }
 
@@ -495,7 +496,7 @@ __global__ void k_tile_list(Grid g, int lo)
 {
     __shared__ int sc[1024];
     const int l = lo + blockIdx.x;
-    const int nt = g.ntx[l] * g.nty[l];
+    const int nt = g.ntx[l] * g.nty[l] * g.ntz[l];
     const uint8_t* fl = g.tflag + g.toff[l];
     const int tid = threadIdx.x, per = (nt + 1023) / 1024;
     const int t0 = tid * per, t1 = min(t0 + per, nt);
@@ -782,15 +783,13 @@ void Launcher::compact(int lo, int hi)
         total += (int)((g.N[l] + NTHREADS - 1) / NTHREADS);
     }
     lbk.base[hi + 1] = total;
-    if (g.d <= 2) cudaMemsetAsync(g.tflag + g.toff[lo], 0, (size_t)(g.toff[hi] - g.toff[lo]) + (size_t)g.ntx[hi] * g.nty[hi], st);
+    cudaMemsetAsync(g.tflag + g.toff[lo], 0,
+                    (size_t)(g.toff[hi] - g.toff[lo]) + (size_t)g.ntx[hi] * g.nty[hi] * g.ntz[hi], st);
     k_cmp_count<<<total, NTHREADS, 0, st>>>(g, lbk, bc);
     k_cmp_scan<<<hi - lo + 1, 1024, 0, st>>>(g, lbk, bc);
     k_cmp_scatter<<<total, NTHREADS, 0, st>>>(g, lbk, bc);
-    n += 3;
-    if (g.d <= 2) {
-        k_tile_list<<<hi - lo + 1, 1024, 0, st>>>(g, lo);
-        ++n;
-    }
+    k_tile_list<<<hi - lo + 1, 1024, 0, st>>>(g, lo);
+    n += 4;
 }
 
 void Launcher::reflux(int lo, int hi)

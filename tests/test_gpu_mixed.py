@@ -78,6 +78,69 @@ def _check(p, q, t):
     return e_mixed, tol
 
 
+def _check_leafwise(p, q, dt, n):
+    """n fine iterations from the same state: identical leaf sets, and every
+    leaf within n * 6 C u32 sigma (|q| + s_v) of the FP64 oracle -- the
+    per-step bound of the module docstring applied leaf by leaf, which a wrong
+    FP32 flux formula (an O(1) relative error in the faces it touches) fails"""
+    pm = p.replace(precision=I.PREC_MIXED)
+    gm, ref = _solver(pm, q), oracle.Oracle(p.replace(precision=I.PREC_FP64), q)
+    gm.iterate(dt, n)
+    ref.iterate(dt, n)
+    kg, vg = gm.leaves()
+    ko, vo = ref.leaves()
+    assert np.array_equal(kg, ko), "leaf sets differ"
+    scale = np.abs(vo).max(axis=0)
+    err = np.abs(vg - vo) / (np.abs(vo) + scale + 1e-300)
+    sigma_eff = dt * _max_speed(p, q) * (1 << p.max_level)
+    tol = n * 6 * C_FLUX * U32 * max(sigma_eff, 1e-3)
+    assert err.max() <= tol, f"max leaf error {err.max():.3e} above {tol:.3e}"
+    assert err.max() > 1e-13, "FP32 flux path not taken"
+    return err.max(), tol
+
+
+def _max_speed(p, q):
+    """largest characteristic speed of the initial data (for the Courant number
+    dt s / dx_L of a fixed dt)"""
+    if p.equation == I.EQ_EULER:
+        g = p.phys[0]
+        m = q.shape[0]
+        rho = q[0]
+        mom = q[1:m - 1]
+        ke = 0.5 * (mom ** 2).sum(axis=0) / rho
+        pr = (g - 1.0) * (q[m - 1] - ke)
+        return float((np.sqrt((mom ** 2).sum(axis=0)) / rho + np.sqrt(g * pr / rho)).max())
+    if p.equation == I.EQ_BURGERS:
+        return float(np.abs(q).max())
+    if p.equation == I.EQ_REACTION_DIFFUSION:  # diffusion number D dt / dx^2, scaled to dx
+        return p.phys[0] * (1 << p.max_level) + p.phys[1] / (1 << p.max_level)
+    return float(np.abs(p.phys[:3]).max())
+
+
+@pytest.mark.parametrize("case", ["burgers1d", "euler2d", "rd2d", "euler3d"])
+def test_mixed_first_iterations_leafwise(case):
+    if case == "burgers1d":
+        p, q = I.burgers_1d(L=10, eps=1e-3)
+        dt = 0.5 / 1024
+    elif case == "euler2d":
+        p, q = I.euler_2d_quadrants(L=7, eps=1e-3, seed=0)
+        dt = 0.5 / 128 / 3.7
+    elif case == "rd2d":
+        p, q = I.rd_bumps_2d(L=7, eps=1e-3, seed=1)
+        dt = 0.2 * (1.0 / 128) ** 2 / 1e-3
+    else:
+        p, q = I.euler_3d_blast(L=5, eps=1e-2, min_level=2)
+        dt = 0.5 / 32 / 4.0
+    _check_leafwise(p, q, dt, 1)
+    _check_leafwise(p, q, dt, 3)
+
+
+def test_mixed_full_size_first_iterations_leafwise():
+    """the 2D Euler L=10 workload: four fine iterations (lmin = 3, 10, 9, 10)"""
+    p, q = I.euler_2d_quadrants(L=10, eps=1e-3, seed=0)
+    _check_leafwise(p, q, 0.5 / 1024 / 3.7, 4)
+
+
 def test_mixed_burgers_1d():
     p, q = I.burgers_1d(L=10, eps=1e-3)
     _check(p, q, 0.3)
