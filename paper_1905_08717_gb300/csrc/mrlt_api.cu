@@ -37,6 +37,16 @@ struct mr_solver {
     double prof_level_ms[LMAX + 1] = {};
     long long prof_launches = 0, prof_all0 = 0;
     unsigned long long work0[(LMAX + 1) * 4] = {};
+    // one macro step (2^{L-min} fine iterations) captured as a CUDA graph and
+    // replayed on `stream`; captured on an internal stream because the legacy
+    // default stream cannot be captured
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t macro_exec = nullptr;
+    long long macro_launches = 0, macro_stage_launches = 0;
+    bool graph_off = false; // capture failed once, or disabled by the caller
+    // batched use: the macro-step finiteness check copies the device error
+    // bits here (pinned host memory) instead of synchronising
+    int* async_err = nullptr;
 };
 
 namespace {
@@ -119,7 +129,7 @@ void drain_events(mr_solver* h)
 
 // one compact RK stage s on the leaves of levels lo..hi (one launch when the
 // levels are independent); dt is the finest-level step
-void stage(mr_solver* h, int lo, int hi, int s, int lmin, double dt)
+void stage(mr_solver* h, int lo, int hi, int s, int lmin)
 {
     const Grid& g = h->K.g;
     static const double b2[2] = {0.5, 0.5};
@@ -131,12 +141,12 @@ void stage(mr_solver* h, int lo, int hi, int s, int lmin, double dt)
         if (h->ev_used * 2 + 2 > (int)h->ev.size()) drain_events(h);
         cudaEventRecord(h->ev[2 * h->ev_used], h->stream);
         h->ev_level[h->ev_used] = hi;
-        launched = launch_stage(g, h->stream, lo, hi, s, lmin, dt, b, reg);
+        launched = launch_stage(g, h->stream, lo, hi, s, lmin, b, reg);
         cudaEventRecord(h->ev[2 * h->ev_used + 1], h->stream);
         ++h->ev_used;
         h->prof_launches += launched > 0 ? launched : 0;
     } else {
-        launched = launch_stage(g, h->stream, lo, hi, s, lmin, dt, b, reg);
+        launched = launch_stage(g, h->stream, lo, hi, s, lmin, b, reg);
     }
     if (launched < 0) {
         h->launch_failed = true;
@@ -171,10 +181,7 @@ mr_status adapt(mr_solver* h, int la)
     Grid& g = h->K.g;
     if (la >= g.L) return MR_OK;
     if (la == g.lb) {
-        unsigned long long init[MMAX];
-        const double tiny = 1e-14;
-        for (int v = 0; v < MMAX; ++v) memcpy(&init[v], &tiny, sizeof tiny);
-        MR_CK(cudaMemcpyAsync(g.scale_bits, init, sizeof init, cudaMemcpyHostToDevice, h->stream));
+        h->K.scale_init();
         for (int l = g.lb; l <= g.L; ++l) h->K.scale(l);
     }
     MR_CK(cudaMemsetAsync(g.flag + g.off[la], 0, (size_t)(h->ntot - g.off[la]), h->stream));
@@ -190,23 +197,22 @@ mr_status lt_iteration(mr_solver* h, long long n, long long nit)
 {
     Grid& g = h->K.g;
     const int L = g.L, lb = g.lb, lmin = level_min(h, n);
-    const double dt = h->dt;
     h->K.leaf_copy(lmin, L, F_QE, F_Q0);
     for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_Q0);
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
         MR_TRY(adapt(h, lmin));
     if (lmin > lb) h->K.project(lmin - 1, PM_MID);
-    stage(h, lmin, L, 1, lmin, dt); // first stage: all active levels at once
+    stage(h, lmin, L, 1, lmin); // first stage: all active levels at once
     for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF2);
     for (int l = L; l >= lmin; --l) {
         if (l < L) h->K.project(l, PM_PRJ2);
-        stage(h, l, l, 2, lmin, dt);
+        stage(h, l, l, 2, lmin);
     }
     if (g.rk == 3) {
         for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF3);
         for (int l = L; l >= lmin; --l) {
             if (l < L) h->K.project(l, PM_PRJ3);
-            stage(h, l, l, 3, lmin, dt);
+            stage(h, l, l, 3, lmin);
         }
     }
     if (h->reg) {
@@ -225,12 +231,12 @@ mr_status gts_iteration(mr_solver* h, long long n)
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
         MR_TRY(adapt(h, lb));
-    stage(h, lb, L, 1, lb, h->dt); // every level at the same instant: one launch per stage
+    stage(h, lb, L, 1, lb); // every level at the same instant: one launch per stage
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q1);
-    stage(h, lb, L, 2, lb, h->dt);
+    stage(h, lb, L, 2, lb);
     if (g.rk == 3) {
         for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q2);
-        stage(h, lb, L, 3, lb, h->dt);
+        stage(h, lb, L, 3, lb);
     }
     return MR_OK;
 }
@@ -238,8 +244,56 @@ mr_status gts_iteration(mr_solver* h, long long n)
 mr_status finite_check(mr_solver* h)
 {
     for (int l = h->K.g.lb; l <= h->K.g.L; ++l) h->K.finite(l);
+    if (h->async_err) {
+        MR_CK(cudaMemcpyAsync(h->async_err, h->K.g.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        return MR_OK;
+    }
     return sync_check(h);
 }
+
+mr_status iteration(mr_solver* h, long long n, long long nit)
+{
+    return h->K.g.gts ? gts_iteration(h, n) : lt_iteration(h, n, nit);
+}
+
+// Capture the nit fine iterations of one macro step as a CUDA graph (stream
+// capture on the internal stream).  Every launch of a macro step is fixed by
+// the layout, the level schedule l_min(n) and the configuration; the fine
+// step is read from g.dtp, so one graph serves every macro step.  Returns
+// false (and leaves nothing captured) when capture is not possible; the
+// caller then launches directly.
+bool capture_macro(mr_solver* h, long long nit)
+{
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    // stage-kernel attributes and occupancy are set up before capture begins
+    if (launch_stage(h->K.g, h->stream, 1, 0, 1, 0, 0.0, 0) < 0) return false;
+    cudaStream_t user = h->stream;
+    const long long n0 = h->K.n, s0 = h->stage_launches;
+    h->stream = h->K.st = h->cap_stream;
+    bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    mr_status r = MR_OK;
+    for (long long i = 0; ok && i < nit && r == MR_OK; ++i) r = iteration(h, i, nit);
+    cudaGraph_t graph = nullptr;
+    if (ok) ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && r == MR_OK && !h->launch_failed;
+    h->stream = h->K.st = user;
+    h->launch_failed = false;
+    if (ok) ok = cudaGraphInstantiate(&h->macro_exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError(); // clear a capture error so that the direct path starts clean
+    h->macro_launches = h->K.n - n0;
+    h->macro_stage_launches = h->stage_launches - s0;
+    h->K.n = n0;
+    h->stage_launches = s0;
+    if (!ok) h->macro_exec = nullptr;
+    return ok;
+}
+
+// Graphs are used for whole macro steps with profiling off, up to 1024 fine
+// iterations per macro step (larger schedules launch directly).
+constexpr long long kMaxGraphIters = 1024;
 
 mr_status run_iters(mr_solver* h, double dt, long long n)
 {
@@ -249,11 +303,29 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
         return MR_E_STATE;
     }
     h->dt = dt;
-    for (long long i = 0; i < n; ++i) {
-        if (h->K.g.gts) MR_TRY(gts_iteration(h, h->pos));
-        else MR_TRY(lt_iteration(h, h->pos, nit));
+    long long i = 0;
+    while (i < n) {
+        if (h->pos == 0) h->K.set_dt(dt);
+        bool graph = h->pos == 0 && n - i >= nit && !h->prof && !h->graph_off && nit <= kMaxGraphIters;
+        if (graph && !h->macro_exec && !capture_macro(h, nit)) {
+            h->graph_off = true; // launch directly from now on
+            graph = false;
+        }
+        if (graph) {
+            MR_CK(cudaGraphLaunch(h->macro_exec, h->stream));
+            h->K.n += h->macro_launches;
+            h->stage_launches += h->macro_stage_launches;
+            h->iters += nit;
+            i += nit;
+            h->pos = 0;
+            ++h->macros;
+            MR_TRY(finite_check(h));
+            continue;
+        }
+        MR_TRY(iteration(h, h->pos, nit));
         ++h->iters;
         ++h->pos;
+        ++i;
         if (h->pos == nit) {
             h->pos = 0;
             ++h->macros;
@@ -264,7 +336,9 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
 }
 
 // CFL step of the finest level: sigma * min(dx_L / max sum_k lambda_k, dx_L^2 / (2 d D))
-mr_status cfl_dt(mr_solver* h, double* dt)
+// CFL reduction (R13), enqueued: the largest sum of characteristic speeds,
+// as a bit pattern, lands in *bits when the stream reaches this point
+mr_status cfl_enqueue(mr_solver* h, unsigned long long* bits)
 {
     Grid& g = h->K.g;
     MR_CK(cudaMemsetAsync(g.wmax, 0, sizeof(unsigned long long), h->stream));
@@ -272,9 +346,15 @@ mr_status cfl_dt(mr_solver* h, double* dt)
         launch_wave(g, h->stream, l);
         ++h->stage_launches;
     }
-    unsigned long long bits = 0;
-    MR_CK(cudaMemcpyAsync(&bits, g.wmax, sizeof bits, cudaMemcpyDeviceToHost, h->stream));
-    MR_TRY(sync_check(h));
+    MR_CK(cudaMemcpyAsync(bits, g.wmax, sizeof *bits, cudaMemcpyDeviceToHost, h->stream));
+    return MR_OK;
+}
+
+// fine step from the largest speed: cfl * dx_L / lambda, and for reaction-
+// diffusion at most the explicit diffusion limit dx^2 / (2 d D)
+double cfl_from_bits(const mr_solver* h, unsigned long long bits)
+{
+    const Grid& g = h->K.g;
     double lam;
     memcpy(&lam, &bits, sizeof lam);
     double dxm = g.dx[g.L][0];
@@ -284,7 +364,15 @@ mr_status cfl_dt(mr_solver* h, double* dt)
         const double dd = dxm * dxm / (2.0 * g.d * g.phys[0]);
         if (lam <= 0.0 || dd < d) d = dd;
     }
-    *dt = h->cfg.cfl * d;
+    return h->cfg.cfl * d;
+}
+
+mr_status cfl_dt(mr_solver* h, double* dt)
+{
+    unsigned long long bits = 0;
+    MR_TRY(cfl_enqueue(h, &bits));
+    MR_TRY(sync_check(h));
+    *dt = cfl_from_bits(h, bits);
     return MR_OK;
 }
 
@@ -384,6 +472,7 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     A(dev_alloc(h, &g.tflag, (size_t)toff));
     A(dev_alloc(h, &g.tlist, (size_t)toff));
     A(dev_alloc(h, &g.scale_bits, MMAX));
+    A(dev_alloc(h, &g.dtp, 1));
     A(dev_alloc(h, &g.err, 1));
     A(dev_alloc(h, &g.near, 1));
     A(dev_alloc(h, &g.wmax, 1));
@@ -655,6 +744,8 @@ mr_status mr_profile(mr_solver* h, int enable)
 void mr_destroy(mr_solver* h)
 {
     if (!h) return;
+    if (h->macro_exec) cudaGraphExecDestroy(h->macro_exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (auto& e : h->ev) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     delete h;

@@ -53,6 +53,7 @@ struct Grid {
     unsigned long long* wmax;
     unsigned long long* updates;
     unsigned long long* work;       // [(LMAX+1) * 4]: leaf-stages per level and stage
+    double* dtp;                    // fine step dt of the current macro step (device scalar)
     long long off[LMAX + 1];
     long long N[LMAX + 1];
     int n[LMAX + 1];
@@ -67,6 +68,37 @@ struct Grid {
     int eps_mode;
     int prec;                       // 0 FP64, 1 mixed: face fluxes in FP32
 };
+
+// Programmatic dependent launch (sm_90 and later).  Every kernel starts by
+// waiting until the kernel before it in the stream has completed and its
+// writes are visible (griddepcontrol.wait), then allows the next kernel's
+// launch to begin (griddepcontrol.launch_dependents).  The launch and the CTA
+// setup of the next kernel thus overlap the tail of this one.  Both are no-ops
+// in a kernel launched without a programmatic dependency.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with programmatic stream serialisation: the kernel may be launched
+// before its predecessor in the stream has finished; it waits in pdl_enter().
+template <class... KArgs, class... Args>
+inline cudaError_t pdl_launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // exposure context: level u being updated, stage s (0 = plain q^n), lmin
 struct Ctx {
@@ -436,9 +468,9 @@ struct Launch; // fwd
 
 // kernel launchers (defined in the .cu files), all on stream `st`
 // one compact RK stage s on every leaf of the levels lo..hi (independent
-// levels only), fine step dt (level u steps dt, or 2^{L-u} dt in LT mode),
-// RK weight b of the stage; returns the number of kernel launches issued
-int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt, double b,
-                 int reg);
+// levels only), fine step dt = *g.dtp (level u steps dt, or 2^{L-u} dt in LT
+// mode), RK weight b of the stage; returns the number of kernel launches issued
+// (-1 when the kernel could not be set up).  lo > hi only sets the kernel up.
+int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg);
 void launch_wave(const Grid& g, cudaStream_t st, int l);
 } // namespace mrlt

@@ -9,6 +9,7 @@ namespace mrlt {
 template <int EQ, int D>
 __global__ void __launch_bounds__(NTHREADS) k_wave(Grid g, int l)
 {
+    pdl_enter();
     constexpr int M = EQ == 2 ? D + 2 : 1;
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
@@ -30,13 +31,13 @@ __global__ void __launch_bounds__(NTHREADS) k_wave(Grid g, int l)
         atomicMax(g.wmax, (unsigned long long)__double_as_longlong(w));
 }
 
-int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt, double b, int reg)
+int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg)
 {
     switch (g.eq) {
-    case 0: return launch_stage_eq<0>(g, st, lo, hi, s, lmin, dt, b, reg);
-    case 1: return launch_stage_eq<1>(g, st, lo, hi, s, lmin, dt, b, reg);
-    case 2: return launch_stage_eq<2>(g, st, lo, hi, s, lmin, dt, b, reg);
-    case 3: return launch_stage_eq<3>(g, st, lo, hi, s, lmin, dt, b, reg);
+    case 0: return launch_stage_eq<0>(g, st, lo, hi, s, lmin, b, reg);
+    case 1: return launch_stage_eq<1>(g, st, lo, hi, s, lmin, b, reg);
+    case 2: return launch_stage_eq<2>(g, st, lo, hi, s, lmin, b, reg);
+    case 3: return launch_stage_eq<3>(g, st, lo, hi, s, lmin, b, reg);
     default: return 0;
     }
 }

@@ -72,26 +72,41 @@ struct TileShape {
     static constexpr size_t SMEM = sizeof(double) * M * NB + sizeof(R) * M * NB + sizeof(R) * M * NF;
 };
 
-// Append, in thread order, the items for which `take` holds to a shared list
-// (warp ballots and a block-wide prefix); every thread of the block calls it
-// with the same `len` and gets the new length.
+// Append, in thread order, `item` to list A where `ta` holds and to list B
+// where `tb` holds, with one barrier per call.  The per-warp counts alternate
+// between two halves of sWarp (2 x 2 x NT/32 ints, selected by `par`): a call
+// may overwrite a half only after every thread has passed the barrier of the
+// call in between, hence after every thread has read that half.  The caller
+// issues a __syncthreads() before reading the lists.
 template <int NT>
-__device__ __forceinline__ int block_append(bool take, int item, short* list, int len, int* sWarp)
+__device__ __forceinline__ void block_append2(bool ta, bool tb, int item, short* la, short* lb, int& na,
+                                              int& nb, int* sWarp, int& par)
 {
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned bal = __ballot_sync(0xffffffffu, take);
-    if (lane == 0) sWarp[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-        const int c = sWarp[w];
-        before += w < warp ? c : 0;
-        total += c;
+    const unsigned ba = __ballot_sync(0xffffffffu, ta);
+    const unsigned bb = __ballot_sync(0xffffffffu, tb);
+    int* w = sWarp + par * 2 * NW;
+    if (lane == 0) {
+        w[warp] = __popc(ba);
+        w[NW + warp] = __popc(bb);
     }
-    if (take) list[len + before + __popc(bal & ((1u << lane) - 1u))] = (short)item;
     __syncthreads();
-    return len + total;
+    int pa = 0, pb = 0, totA = 0, totB = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        const int ca = w[i], cb = w[NW + i];
+        pa += i < warp ? ca : 0;
+        pb += i < warp ? cb : 0;
+        totA += ca;
+        totB += cb;
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (ta) la[na + pa + __popc(ba & below)] = (short)item;
+    if (tb) lb[nb + pb + __popc(bb & below)] = (short)item;
+    na += totA;
+    nb += totB;
+    par ^= 1;
 }
 
 // Tiled stage (d = 1, 2, 3).  The CTA
@@ -110,8 +125,10 @@ __device__ __forceinline__ int block_append(bool take, int item, short* list, in
 // Work lists keep every warp on one kind of work.
 template <int EQ, int D, class R>
 __global__ void __launch_bounds__(Tile<D>::TX * Tile<D>::TY * Tile<D>::TZ)
-k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, int reg)
+k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
 {
+    pdl_enter();
+    const double dt = *g.dtp; // fine step of the macro step
     using S = TileShape<EQ, D, R>;
     constexpr int M = S::M, TX = S::TX, TY = S::TY, TZ = S::TZ, NT = S::NT, H = S::H;
     constexpr int BX = S::BX, BY = S::BY, NB = S::NB;
@@ -126,8 +143,8 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
     // x faces [0, NFX), y faces [NFX, NFX + NFY), z faces [NFX + NFY, NF)
     R (*sF)[NF] = reinterpret_cast<R (*)[NF]>(smem + (sizeof(double) + sizeof(R)) * M * NB);
     __shared__ uint8_t sSt[NB];
-    __shared__ short sList[NL];
-    __shared__ int sWarp[NT / 32];
+    __shared__ short sList[NL], sList2[NL];
+    __shared__ int sWarp[4 * (NT / 32)];
 
     // The CTA walks the active tiles (tiles holding a leaf) of levels lo..hi,
     // in level order; one launch may cover several independent levels.
@@ -236,19 +253,18 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
         atomicAdd(&g.work[u * 4 + s], (unsigned long long)nleaf);
     }
 
-    // 2. exposures of the needed cells: stored nodes, then the others
-    int nst = 0;
+    // 2. exposures of the needed cells: stored nodes (list 1), then virtual
+    //    cells and ghosts (list 2)
+    int nst = 0, nvc = 0, par = 0;
     for (int b0 = 0; b0 < NB; b0 += NT) {
         const int b = b0 + tid;
-        nst = block_append<NT>(b < NB && (sSt[b] == 1 || sSt[b] == 2) && needed(b), b, sList, nst, sWarp);
+        const bool nd = b < NB && needed(b);
+        const bool stored = nd && (sSt[b] == 1 || sSt[b] == 2);
+        block_append2<NT>(stored, nd && !stored, b, sList, sList2, nst, nvc, sWarp, par);
     }
-    int ncell = nst;
-    for (int b0 = 0; b0 < NB; b0 += NT) {
-        const int b = b0 + tid;
-        ncell = block_append<NT>(b < NB && sSt[b] != 1 && sSt[b] != 2 && needed(b), b, sList, ncell, sWarp);
-    }
-    for (int t = tid; t < ncell; t += NT) {
-        const int b = sList[t];
+    __syncthreads();
+    for (int t = tid; t < nst + nvc; t += NT) {
+        const int b = t < nst ? sList[t] : sList2[t - nst];
         const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
         double W[M];
         R P[M];
@@ -271,52 +287,29 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
     }
     __syncthreads();
 
-    // 3a. plain faces on level u
-    int nfl = 0;
+    // 3. the faces touching a tile leaf, one pass: faces of a leaf against an
+    //    internal node (list 1, 2^{d-1} sub-face tasks each, in adjacent
+    //    lanes), then plain faces on level u (list 2), one thread per face
+    int nsb = 0, nfl = 0;
     for (int f0 = 0; f0 < NF; f0 += NT) {
         const int f = f0 + tid;
-        bool take = false;
+        bool sub = false, plain = false;
         if (f < NF) {
             int k, lo, hi;
             bool lL, lH;
             face(f, k, lo, hi, lL, lH);
-            const bool sub = finer && ((lL && sSt[hi] == 2) || (lH && sSt[lo] == 2));
-            take = (lL || lH) && !sub;
+            sub = finer && ((lL && sSt[hi] == 2) || (lH && sSt[lo] == 2));
+            plain = (lL || lH) && !sub;
         }
-        nfl = block_append<NT>(take, f, sList, nfl, sWarp);
-    }
-    for (int t = tid; t < nfl; t += NT) {
-        const int f = sList[t];
-        int k, lo, hi;
-        bool lL, lH;
-        face(f, k, lo, hi, lL, lH);
-        const int stride = k == 0 ? 1 : (k == 1 ? SY : SZ);
-        R F[M];
-        flux_recon<EQ, D, M, R>(g, k, g.dx[u][k], [&](int c, int v) { return sP[v][lo + (c - 1) * stride]; }, F);
-#pragma unroll
-        for (int v = 0; v < M; ++v) sF[v][f] = F[v];
+        block_append2<NT>(sub, plain, f, sList, sList2, nsb, nfl, sWarp, par);
     }
     __syncthreads();
-
-    // 3b. faces of a leaf against an internal node: one thread per sub-face
-    int nsb = 0;
-    if (finer) {
-        for (int f0 = 0; f0 < NF; f0 += NT) {
-            const int f = f0 + tid;
-            bool take = false;
-            if (f < NF) {
-                int k, lo, hi;
-                bool lL, lH;
-                face(f, k, lo, hi, lL, lH);
-                take = (lL && sSt[hi] == 2) || (lH && sSt[lo] == 2);
-            }
-            nsb = block_append<NT>(take, f, sList, nsb, sWarp);
-        }
-    }
-    for (int base = 0; base < nsb * NTS; base += NT) {
+    const int nsub = nsb * NTS; // sub-face tasks come first; NTS divides 32
+    for (int base = 0; base < nsub + nfl; base += NT) {
         const int task = base + tid;
-        const bool act = task < nsb * NTS;
-        const int f = act ? sList[task / NTS] : 0, t = task % NTS;
+        const bool isSub = task < nsub, act = task < nsub + nfl;
+        const int f = isSub ? sList[task / NTS] : (act ? sList2[task - nsub] : 0);
+        const int t = isSub ? task % NTS : 0;
         R F[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) F[v] = R(0);
@@ -324,58 +317,68 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double dt, double bstage, 
             int k, lo, hi;
             bool lL, lH;
             face(f, k, lo, hi, lL, lH);
-            const bool leafIsLo = lL && sSt[hi] == 2;
-            const int bl = leafIsLo ? lo : hi, side = leafIsLo ? 1 : -1;
-            const int bx = bl % BX, by = (bl / BX) % BY, bz = bl / SZ;
-            const int c[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, D > 2 ? oz + bz - H : 0};
-            // tangential directions of the face, in increasing order; sub-face
-            // t takes child offset (t & 1) along the first, (t >> 1) along the second
-            const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
-            R P4[4][M];
+            if (!isSub) {
+                const int stride = k == 0 ? 1 : (k == 1 ? SY : SZ);
+                flux_recon<EQ, D, M, R>(g, k, g.dx[u][k], [&](int c, int v) { return sP[v][lo + (c - 1) * stride]; },
+                                        F);
+            } else {
+                const bool leafIsLo = lL && sSt[hi] == 2;
+                const int bl = leafIsLo ? lo : hi, side = leafIsLo ? 1 : -1;
+                const int bx = bl % BX, by = (bl / BX) % BY, bz = bl / SZ;
+                const int c[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, D > 2 ? oz + bz - H : 0};
+                // tangential directions of the face, in increasing order; sub-face
+                // t takes child offset (t & 1) along the first, (t >> 1) along the second
+                const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+                R P4[4][M];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                // stencil cell i on level u+1; the leaf's own children are virtual
-                int p[3] = {0, 0, 0};
-                p[k] = 2 * c[k] + (side > 0 ? i : i - 2);
-                if (D > 1) p[j1] = 2 * c[j1] + (t & 1);
-                if (D > 2) p[j2] = 2 * c[j2] + (t >> 1);
-                const bool own = side > 0 ? i < 2 : i >= 2;
-                double W[M];
-                if (own) {
-                    const int ax = p[0] & 1, ay = p[1] & 1, az = p[2] & 1;
+                for (int i = 0; i < 4; ++i) {
+                    // stencil cell i on level u+1; the leaf's own children are virtual
+                    int p[3] = {0, 0, 0};
+                    p[k] = 2 * c[k] + (side > 0 ? i : i - 2);
+                    if (D > 1) p[j1] = 2 * c[j1] + (t & 1);
+                    if (D > 2) p[j2] = 2 * c[j2] + (t >> 1);
+                    const bool own = side > 0 ? i < 2 : i >= 2;
+                    double W[M];
+                    if (own) {
+                        const int ax = p[0] & 1, ay = p[1] & 1, az = p[2] & 1;
 #pragma unroll
-                    for (int v = 0; v < M; ++v) W[v] = 0.0;
+                        for (int v = 0; v < M; ++v) W[v] = 0.0;
 #pragma unroll
-                    for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz)
+                        for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz)
 #pragma unroll
-                        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
+                            for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
 #pragma unroll
-                            for (int dx = -1; dx <= 1; ++dx) {
-                                const double w = ((D > 2 ? pw(az, dz) : 1.0) * (D > 1 ? pw(ay, dy) : 1.0)) *
-                                                 pw(ax, dx);
-                                const int bs = bl + dz * SZ + dy * SY + dx;
+                                for (int dx = -1; dx <= 1; ++dx) {
+                                    const double w = ((D > 2 ? pw(az, dz) : 1.0) * (D > 1 ? pw(ay, dy) : 1.0)) *
+                                                     pw(ax, dx);
+                                    const int bs = bl + dz * SZ + dy * SY + dx;
 #pragma unroll
-                                for (int v = 0; v < M; ++v) W[v] += w * sW[v][bs];
-                            }
-                } else {
-                    value_at<D, M>(g, x, u + 1, p, W);
+                                    for (int v = 0; v < M; ++v) W[v] += w * sW[v][bs];
+                                }
+                    } else {
+                        value_at<D, M>(g, x, u + 1, p, W);
+                    }
+                    recon_vars<EQ, D, M, R>(g, W, P4[i]);
                 }
-                recon_vars<EQ, D, M, R>(g, W, P4[i]);
+                flux_recon<EQ, D, M, R>(g, k, g.dx[u + 1][k], [&](int cc, int v) { return P4[cc][v]; }, F);
             }
-            flux_recon<EQ, D, M, R>(g, k, g.dx[u + 1][k], [&](int cc, int v) { return P4[cc][v]; }, F);
         }
-        if constexpr (NTS == 2) { // the two sub-faces of a face sit in lanes 2i, 2i+1
+        // mean of the sub-face fluxes of a face (every lane takes part in the
+        // shuffles; plain-face lanes keep their own flux)
+        if constexpr (NTS == 2) {
 #pragma unroll
             for (int v = 0; v < M; ++v) {
                 const R other = __shfl_xor_sync(0xffffffffu, F[v], 1);
-                if (act && t == 0) sF[v][f] = (F[v] + other) * R(0.5);
+                if (isSub && t == 0) sF[v][f] = (F[v] + other) * R(0.5);
+                else if (act && !isSub) sF[v][f] = F[v];
             }
-        } else if constexpr (NTS == 4) { // lanes 4i .. 4i+3
+        } else if constexpr (NTS == 4) {
 #pragma unroll
             for (int v = 0; v < M; ++v) {
                 const R pair = F[v] + __shfl_xor_sync(0xffffffffu, F[v], 1);
                 const R quad = pair + __shfl_xor_sync(0xffffffffu, pair, 2);
-                if (act && t == 0) sF[v][f] = quad * R(0.25);
+                if (isSub && t == 0) sF[v][f] = quad * R(0.25);
+                else if (act && !isSub) sF[v][f] = F[v];
             }
         } else if (act) {
 #pragma unroll
@@ -444,8 +447,7 @@ static inline int grid_for(const Grid& g, int l)
 // the persistent grid is the device's resident capacity for this instantiation
 // (occupancy API, once per device), capped by the tile count.
 template <int EQ, int D, class R>
-static int stage_dispatch(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt,
-                          double b, int reg)
+static int stage_dispatch(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg)
 {
     using S = TileShape<EQ, D, R>;
     constexpr int kMaxDev = 64;
@@ -463,21 +465,23 @@ static int stage_dispatch(const Grid& g, cudaStream_t st, int lo, int hi, int s,
             return -1;
         resident[dev] = per_sm * sms;
     }
+    if (lo > hi) return 0; // set-up only
     long long total = 0;
     for (int l = lo; l <= hi; ++l) total += (long long)g.ntx[l] * g.nty[l] * g.ntz[l];
     const long long grid = total < resident[dev] ? total : resident[dev];
-    k_stage_tile<EQ, D, R><<<(unsigned)grid, S::NT, S::SMEM, st>>>(g, lo, hi, s, lmin, dt, b, reg);
+    // launched without a programmatic dependency: the persistent grid assigns
+    // tiles statically, so it must find the SMs free to be resident at once
+    k_stage_tile<EQ, D, R><<<(unsigned)grid, S::NT, S::SMEM, st>>>(g, lo, hi, s, lmin, b, reg);
     return 1;
 }
 
 // stage launcher of one equation (all dimensions, both precisions); each is
 // defined in its own translation unit so that they compile in parallel
 template <int EQ>
-int launch_stage_eq(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt, double b,
-                    int reg);
-template <> int launch_stage_eq<0>(const Grid&, cudaStream_t, int, int, int, int, double, double, int);
-template <> int launch_stage_eq<1>(const Grid&, cudaStream_t, int, int, int, int, double, double, int);
-template <> int launch_stage_eq<2>(const Grid&, cudaStream_t, int, int, int, int, double, double, int);
-template <> int launch_stage_eq<3>(const Grid&, cudaStream_t, int, int, int, int, double, double, int);
+int launch_stage_eq(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg);
+template <> int launch_stage_eq<0>(const Grid&, cudaStream_t, int, int, int, int, double, int);
+template <> int launch_stage_eq<1>(const Grid&, cudaStream_t, int, int, int, int, double, int);
+template <> int launch_stage_eq<2>(const Grid&, cudaStream_t, int, int, int, int, double, int);
+template <> int launch_stage_eq<3>(const Grid&, cudaStream_t, int, int, int, int, double, int);
 
 } // namespace mrlt

@@ -10,20 +10,20 @@
 namespace mrlt {
 
 template <>
-int launch_stage_eq<MRLT_STAGE_EQ>(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double dt,
-                                   double b, int reg)
+int launch_stage_eq<MRLT_STAGE_EQ>(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b,
+                                   int reg)
 {
     constexpr int E = MRLT_STAGE_EQ;
     switch (g.d) {
     case 1:
-        return g.prec ? stage_dispatch<E, 1, float>(g, st, lo, hi, s, lmin, dt, b, reg)
-                      : stage_dispatch<E, 1, double>(g, st, lo, hi, s, lmin, dt, b, reg);
+        return g.prec ? stage_dispatch<E, 1, float>(g, st, lo, hi, s, lmin, b, reg)
+                      : stage_dispatch<E, 1, double>(g, st, lo, hi, s, lmin, b, reg);
     case 2:
-        return g.prec ? stage_dispatch<E, 2, float>(g, st, lo, hi, s, lmin, dt, b, reg)
-                      : stage_dispatch<E, 2, double>(g, st, lo, hi, s, lmin, dt, b, reg);
+        return g.prec ? stage_dispatch<E, 2, float>(g, st, lo, hi, s, lmin, b, reg)
+                      : stage_dispatch<E, 2, double>(g, st, lo, hi, s, lmin, b, reg);
     case 3:
-        return g.prec ? stage_dispatch<E, 3, float>(g, st, lo, hi, s, lmin, dt, b, reg)
-                      : stage_dispatch<E, 3, double>(g, st, lo, hi, s, lmin, dt, b, reg);
+        return g.prec ? stage_dispatch<E, 3, float>(g, st, lo, hi, s, lmin, b, reg)
+                      : stage_dispatch<E, 3, double>(g, st, lo, hi, s, lmin, b, reg);
     default:
         return 0;
     }

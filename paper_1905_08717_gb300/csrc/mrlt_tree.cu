@@ -24,6 +24,7 @@ static inline int blocks_list(const Grid& g, int l)
 // ------------------------------------------------------------ simple leaf copies
 __global__ void k_leaf_copy(Grid g, int lo, int hi, int from, int to)
 {
+    pdl_enter();
     for (int l = lo; l <= hi; ++l) {
         const int cnt = g.counts[l];
         const int* list = g.leaves + g.off[l];
@@ -54,6 +55,7 @@ __global__ void k_leaf_copy(Grid g, int lo, int hi, int from, int to)
 template <int D>
 __global__ void k_project(Grid g, int l, int mode)
 {
+    pdl_enter();
     const int cnt = g.counts[LMAX + 1 + l];
     const int* list = g.inner + g.off[l];
     const long long N = g.N[l], Nc = g.N[l + 1];
@@ -151,6 +153,7 @@ __device__ __forceinline__ double eps_level(const Grid& g, int l)
 template <int D, int M>
 __global__ void k_detail(Grid g, int lo, int hi)
 {
+    pdl_enter();
     double sc[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) sc[v] = __longlong_as_double((long long)g.scale_bits[v]);
@@ -217,6 +220,7 @@ __device__ __forceinline__ bool nb3(const Grid& g, int l, const int c[3], int dx
 template <int D>
 __global__ void k_desire(Grid g, int lo, int hi, int la)
 {
+    pdl_enter();
     for (int l = lo; l <= hi; ++l) {
         const long long N = g.N[l];
         uint8_t* fl = g.flag + g.off[l];
@@ -252,6 +256,7 @@ __global__ void k_desire(Grid g, int lo, int hi, int la)
 template <int D>
 __global__ void k_allow(Grid g, int lo, int hi, int la)
 {
+    pdl_enter();
     for (int l = lo; l <= hi; ++l) {
         const long long N = g.N[l];
         uint8_t* fl = g.flag + g.off[l];
@@ -301,6 +306,7 @@ __global__ void k_allow(Grid g, int lo, int hi, int la)
 template <int D>
 __global__ void k_close(Grid g, int l)
 {
+    pdl_enter();
     const int pl = l - 1;
     const long long N = g.N[pl];
     uint8_t* fp = g.flag + g.off[pl];
@@ -333,6 +339,7 @@ __global__ void k_close(Grid g, int l)
 template <int D, int M>
 __global__ void k_apply(Grid g, int l, int la)
 {
+    pdl_enter();
     const long long N = g.N[l];
     GRID_STRIDE(id, N)
     {
@@ -390,6 +397,7 @@ __device__ __forceinline__ int block_level(const LevelBlocks& b, int blk)
 
 __global__ void k_cmp_count(Grid g, LevelBlocks lbk, int* bc)
 {
+    pdl_enter();
     const int l = block_level(lbk, blockIdx.x);
     const long long N = g.N[l];
     const long long i = (long long)(blockIdx.x - lbk.base[l]) * blockDim.x + threadIdx.x;
@@ -417,6 +425,7 @@ __global__ void k_cmp_count(Grid g, LevelBlocks lbk, int* bc)
 // exclusive scan of the per-block counts, one block per level; totals to counts[l]
 __global__ void k_cmp_scan(Grid g, LevelBlocks lbk, int* bc)
 {
+    pdl_enter();
     __shared__ int sa[1024], sb[1024];
     const int l = lbk.lo + blockIdx.x;
     const int b0l = lbk.base[l], nb = lbk.base[l + 1] - b0l;
@@ -455,6 +464,7 @@ __global__ void k_cmp_scan(Grid g, LevelBlocks lbk, int* bc)
 
 __global__ void k_cmp_scatter(Grid g, LevelBlocks lbk, const int* bc)
 {
+    pdl_enter();
     const int l = block_level(lbk, blockIdx.x);
     const long long N = g.N[l];
     const long long i = (long long)(blockIdx.x - lbk.base[l]) * blockDim.x + threadIdx.x;
@@ -494,6 +504,7 @@ __global__ void k_cmp_scatter(Grid g, LevelBlocks lbk, const int* bc)
 // ordered list of the active tiles of level lo + blockIdx.x (one block per level)
 __global__ void k_tile_list(Grid g, int lo)
 {
+    pdl_enter();
     __shared__ int sc[1024];
     const int l = lo + blockIdx.x;
     const int nt = g.ntx[l] * g.nty[l] * g.ntz[l];
@@ -523,6 +534,7 @@ __global__ void k_tile_list(Grid g, int lo)
 template <int D>
 __global__ void k_reflux(Grid g, int lo, int hi)
 {
+    pdl_enter();
   for (int l = lo; l <= hi; ++l) {
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
@@ -581,6 +593,7 @@ __global__ void k_reflux(Grid g, int lo, int hi)
 // ------------------------------------------------------------ reductions
 __global__ void k_scale(Grid g, int l)
 {
+    pdl_enter();
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
     const long long N = g.N[l];
@@ -601,6 +614,7 @@ __global__ void k_scale(Grid g, int l)
 
 __global__ void k_finite(Grid g, int l)
 {
+    pdl_enter();
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
     const long long N = g.N[l];
@@ -616,6 +630,7 @@ __global__ void k_finite(Grid g, int l)
 // fixed-shape partial sums (deterministic): part[block * m + v]
 __global__ void k_mass(Grid g, int l, double* part)
 {
+    pdl_enter();
     __shared__ double sh[NTHREADS];
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
@@ -640,6 +655,7 @@ __global__ void k_mass(Grid g, int l, double* part)
 
 __global__ void k_pack(Grid g, int l, long long base, int* keys, double* vals)
 {
+    pdl_enter();
     const int cnt = g.counts[l];
     const int* list = g.leaves + g.off[l];
     const long long N = g.N[l];
@@ -667,6 +683,7 @@ __global__ void k_pack(Grid g, int l, long long base, int* keys, double* vals)
 template <int D>
 __global__ void k_uni_up(Grid g, int l, double* T, uint8_t* us)
 {
+    pdl_enter();
     const long long N = g.N[l];
     const long long Nc = l < g.L ? g.N[l + 1] : 0;
     double* Tl = T + g.off[l] * g.m;
@@ -694,6 +711,7 @@ __global__ void k_uni_up(Grid g, int l, double* T, uint8_t* us)
 template <int D>
 __global__ void k_uni_down(Grid g, int l, double* T, uint8_t* us)
 {
+    pdl_enter();
     const long long N = g.N[l], Np = g.N[l - 1];
     double* Tl = T + g.off[l] * g.m;
     const double* Tp = T + g.off[l - 1] * g.m;
@@ -723,7 +741,7 @@ __global__ void k_uni_down(Grid g, int l, double* T, uint8_t* us)
 template <int D>
 static void project_d(Launcher& L, int l, int mode)
 {
-    k_project<D><<<blocks_list(L.g, l), NTHREADS, 0, L.st>>>(L.g, l, mode);
+    pdl_launch(k_project<D>, blocks_list(L.g, l), NTHREADS, 0, L.st, L.g, l, mode);
 }
 
 void Launcher::project(int l, int mode)
@@ -737,7 +755,7 @@ void Launcher::project(int l, int mode)
 void Launcher::leaf_copy(int lo, int hi, int from, int to)
 {
     ++n;
-    k_leaf_copy<<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi, from, to);
+    pdl_launch(k_leaf_copy, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi, from, to);
 }
 
 template <int D, int M>
@@ -745,18 +763,18 @@ static void adapt_dm(Launcher& L, int la)
 {
     const Grid& g = L.g;
     const int hi = g.L - 1; // levels whose nodes may own children
-    k_detail<D, M><<<blocks_list(g, hi), NTHREADS, 0, L.st>>>(g, la, hi);
-    k_desire<D><<<blocks_dense(g.N[hi]), NTHREADS, 0, L.st>>>(g, la, hi, la);
-    k_allow<D><<<blocks_dense(g.N[hi]), NTHREADS, 0, L.st>>>(g, la, hi, la);
+    pdl_launch(k_detail<D, M>, blocks_list(g, hi), NTHREADS, 0, L.st, g, la, hi);
+    pdl_launch(k_desire<D>, blocks_dense(g.N[hi]), NTHREADS, 0, L.st, g, la, hi, la);
+    pdl_launch(k_allow<D>, blocks_dense(g.N[hi]), NTHREADS, 0, L.st, g, la, hi, la);
     L.n += 3;
-    for (int l = g.L - 1; l > la; --l, ++L.n) k_close<D><<<blocks_dense(g.N[l - 1]), NTHREADS, 0, L.st>>>(g, l);
+    for (int l = g.L - 1; l > la; --l, ++L.n) pdl_launch(k_close<D>, blocks_dense(g.N[l - 1]), NTHREADS, 0, L.st, g, l);
 }
 
 template <int D, int M>
 static void apply_dm(Launcher& L, int la)
 {
     const Grid& g = L.g;
-    for (int l = la; l <= g.L; ++l, ++L.n) k_apply<D, M><<<blocks_dense(g.N[l]), NTHREADS, 0, L.st>>>(g, l, la);
+    for (int l = la; l <= g.L; ++l, ++L.n) pdl_launch(k_apply<D, M>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
 }
 
 #define MRLT_DM_DISPATCH(fn, ...)                                   \
@@ -785,19 +803,43 @@ void Launcher::compact(int lo, int hi)
     lbk.base[hi + 1] = total;
     cudaMemsetAsync(g.tflag + g.toff[lo], 0,
                     (size_t)(g.toff[hi] - g.toff[lo]) + (size_t)g.ntx[hi] * g.nty[hi] * g.ntz[hi], st);
-    k_cmp_count<<<total, NTHREADS, 0, st>>>(g, lbk, bc);
-    k_cmp_scan<<<hi - lo + 1, 1024, 0, st>>>(g, lbk, bc);
-    k_cmp_scatter<<<total, NTHREADS, 0, st>>>(g, lbk, bc);
-    k_tile_list<<<hi - lo + 1, 1024, 0, st>>>(g, lo);
+    pdl_launch(k_cmp_count, total, NTHREADS, 0, st, g, lbk, bc);
+    pdl_launch(k_cmp_scan, hi - lo + 1, 1024, 0, st, g, lbk, bc);
+    pdl_launch(k_cmp_scatter, total, NTHREADS, 0, st, g, lbk, (const int*)bc);
+    pdl_launch(k_tile_list, hi - lo + 1, 1024, 0, st, g, lo);
     n += 4;
 }
 
 void Launcher::reflux(int lo, int hi)
 {
     ++n;
-    if (g.d == 1) k_reflux<1><<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi);
-    else if (g.d == 2) k_reflux<2><<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi);
-    else k_reflux<3><<<blocks_list(g, hi), NTHREADS, 0, st>>>(g, lo, hi);
+    if (g.d == 1) pdl_launch(k_reflux<1>, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi);
+    else if (g.d == 2) pdl_launch(k_reflux<2>, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi);
+    else pdl_launch(k_reflux<3>, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi);
+}
+
+__global__ void k_scale_init(Grid g)
+{
+    pdl_enter();
+    if (threadIdx.x < MMAX) g.scale_bits[threadIdx.x] = (unsigned long long)__double_as_longlong(1e-14);
+}
+
+__global__ void k_set_dt(Grid g, double dt)
+{
+    pdl_enter();
+    if (threadIdx.x == 0) *g.dtp = dt;
+}
+
+void Launcher::scale_init()
+{
+    pdl_launch(k_scale_init, 1, 32, 0, st, g);
+    ++n;
+}
+
+void Launcher::set_dt(double dt)
+{
+    pdl_launch(k_set_dt, 1, 32, 0, st, g, dt);
+    ++n;
 }
 
 void Launcher::scale(int l)

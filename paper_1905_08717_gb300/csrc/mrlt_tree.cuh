@@ -20,6 +20,8 @@ struct Launcher {
     void compact(int lo, int hi);                      // leaf / node / tile lists of levels lo..hi
     void reflux(int lo, int hi);                       // coarse levels lo..hi
     void scale(int l);
+    void scale_init();                                 // running max |q_v| := 1e-14
+    void set_dt(double dt);                            // *g.dtp := dt
     void finite(int l);
     void mass(int l, double* part);
     void pack(int l, long long base, int* keys, double* vals);
