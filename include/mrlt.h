@@ -180,6 +180,43 @@ const char* mr_last_error(const mr_solver* h);
 /* Number of kernel launches issued by this handle since creation. */
 long long mr_launch_count(const mr_solver* h);
 
+/* ---- Batched instances --------------------------------------------------
+ * Many independent problems (each its own configuration, level range and
+ * initial data) advanced together.  The paper treats one problem at a time;
+ * batching is this library's way of filling a GPU with problems that are
+ * each too small for it.  Every instance is an ordinary solver with its own
+ * device memory and its own internal CUDA stream; one macro step of an
+ * instance is a CUDA graph (captured once per instance), so the instances'
+ * kernels overlap on the GPU while the host only picks each instance's CFL
+ * step (Sec. 4, Eq. 13) and launches its graph. */
+typedef struct mr_batch mr_batch;
+
+/* Create n >= 1 instances from cfgs[i] and the finest-level data q0s[i] (each
+ * as for mr_create).  The batch orders its work after the work already
+ * enqueued on cuda_stream at each call, and each call returns after all of its
+ * work has completed.  On failure nothing is left allocated and *out is NULL;
+ * *failed_index (may be NULL) receives the instance that failed, or -1. */
+mr_status mr_batch_create(int n, const mr_config* cfgs, const double* const* q0s, void* cuda_stream,
+                          mr_batch** out, int* failed_index);
+
+/* Advance every instance to t_target as mr_step does (whole macro steps of its
+ * own CFL step, the last shortened), all instances concurrently.  Every
+ * instance must be at a macro-step boundary.  *iters_out (may be NULL)
+ * receives the fine iterations done, summed over instances.  On an error the
+ * failing instance is reported by mr_batch_last_error. */
+mr_status mr_batch_step(mr_batch* b, double t_target, long long* iters_out);
+
+/* Instance i (0 <= i < n), owned by the batch: use it with mr_read,
+ * mr_last_error and mr_launch_count; NULL if i is out of range.  Do not destroy
+ * it, and do not step it while the batch is stepping. */
+mr_solver* mr_batch_instance(mr_batch* b, int i);
+
+/* Reason for the last failure of a batch call. */
+const char* mr_batch_last_error(const mr_batch* b);
+
+/* Release the batch and all its instances (NULL is ignored). */
+void mr_batch_destroy(mr_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,8 +69,18 @@ def library() -> ctypes.CDLL:
         lib.mr_leaf_mass_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double), vp, vp, ll, ctypes.c_int,
                                              vp, vp, ctypes.c_char_p, ctypes.c_size_t]
+        lib.mr_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(mr_config),
+                                        ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), vp,
+                                        ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)]
+        lib.mr_batch_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ll)]
+        lib.mr_batch_instance.argtypes = [vp, ctypes.c_int]
+        lib.mr_batch_instance.restype = vp
+        lib.mr_batch_last_error.argtypes = [vp]
+        lib.mr_batch_last_error.restype = ctypes.c_char_p
+        lib.mr_batch_destroy.argtypes = [vp]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
-                     "mr_iterate", "mr_read", "mr_leaf_mass_noalloc"):
+                     "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create",
+                     "mr_batch_step"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -132,11 +142,24 @@ class Solver:
         if r != 0:
             raise MRError(r, "mr_create failed")
 
+    @classmethod
+    def _view(cls, problem, handle: int, owner):
+        """non-owning view of a solver that `owner` (a Batch) holds"""
+        self = cls.__new__(cls)
+        self.p = problem
+        self.m = problem.nvars()
+        self._h = ctypes.c_void_p(handle)
+        self._owner = owner
+        return self
+
     def _check(self, r: int, what: str):
         if r != 0:
             raise MRError(r, f"{what}: {library().mr_last_error(self._h).decode()}")
 
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self._h = ctypes.c_void_p()  # a view: the batch releases the solver
+            return
         if self._h:
             library().mr_destroy(self._h)
             self._h = ctypes.c_void_p()
@@ -210,3 +233,49 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(library().mr_launch_count(self._h))
+
+
+class Batch:
+    """Independent problems advanced together (C-ABI `mr_batch`): each
+    instance is a solver with its own stream and its macro step as a CUDA
+    graph, so the instances run concurrently on the GPU."""
+
+    def __init__(self, problems, q0s, stream=None):
+        lib = library()
+        if len(problems) != len(q0s) or not problems:
+            raise ValueError("one initial condition per problem, at least one problem")
+        self.problems = list(problems)
+        n = len(problems)
+        cfgs = (mr_config * n)(*[make_config(p) for p in problems])
+        self._q = [np.ascontiguousarray(q, dtype=np.float64).reshape(p.nvars(), -1)
+                   for p, q in zip(problems, q0s)]
+        ptrs = (ctypes.POINTER(ctypes.c_double) * n)(*[_dptr(q) for q in self._q])
+        self._b = ctypes.c_void_p()
+        bad = ctypes.c_int(-1)
+        r = lib.mr_batch_create(n, cfgs, ptrs, ctypes.c_void_p(_stream_handle(stream)),
+                                ctypes.byref(self._b), ctypes.byref(bad))
+        if r != 0:
+            raise MRError(r, f"mr_batch_create failed (instance {bad.value})")
+        self.instances = [Solver._view(p, lib.mr_batch_instance(self._b, i), self)
+                          for i, p in enumerate(problems)]
+
+    def step(self, t_target: float) -> int:
+        lib = library()
+        it = ctypes.c_longlong()
+        r = lib.mr_batch_step(self._b, t_target, ctypes.byref(it))
+        if r != 0:
+            raise MRError(r, "batch step: " + lib.mr_batch_last_error(self._b).decode())
+        return it.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for v in self.instances:
+                v._h = ctypes.c_void_p()
+            library().mr_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -756,3 +756,152 @@ const char* mr_last_error(const mr_solver* h) { return h ? h->err.c_str() : kNul
 long long mr_launch_count(const mr_solver* h) { return h ? h->K.n + h->stage_launches : 0; }
 
 } // extern "C"
+
+// ---------------------------------------------------------------- batches
+struct mr_batch {
+    std::vector<mr_solver*> inst;
+    std::vector<cudaStream_t> streams;  // one internal stream per instance
+    std::vector<cudaEvent_t> ev;        // per instance: its CFL value has arrived
+    cudaStream_t user = nullptr;
+    cudaEvent_t join = nullptr;
+    unsigned long long* bits = nullptr; // pinned: largest speed per instance
+    int* errs = nullptr;                // pinned: device error bits per instance
+    std::string err;
+};
+
+namespace {
+
+void batch_free(mr_batch* b)
+{
+    for (mr_solver* h : b->inst) mr_destroy(h);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->bits) cudaFreeHost(b->bits);
+    if (b->errs) cudaFreeHost(b->errs);
+    delete b;
+}
+
+mr_status batch_fail(mr_batch* b, int i, mr_status r)
+{
+    char buf[64];
+    snprintf(buf, sizeof buf, "instance %d: ", i);
+    b->err = std::string(buf) + (i >= 0 && i < (int)b->inst.size() ? b->inst[i]->err : std::string(""));
+    return r;
+}
+
+} // namespace
+
+extern "C" {
+
+mr_status mr_batch_create(int n, const mr_config* cfgs, const double* const* q0s, void* cuda_stream,
+                          mr_batch** out, int* failed_index)
+{
+    if (failed_index) *failed_index = -1;
+    if (!out) return MR_E_INVALID;
+    *out = nullptr;
+    if (n < 1 || !cfgs || !q0s) return MR_E_INVALID;
+    mr_batch* b = new (std::nothrow) mr_batch();
+    if (!b) return MR_E_NOMEM;
+    b->user = (cudaStream_t)cuda_stream;
+    auto fail = [&](int i, mr_status r) {
+        if (failed_index) *failed_index = i;
+        batch_free(b);
+        return r;
+    };
+    if (cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost((void**)&b->bits, sizeof(unsigned long long) * n) != cudaSuccess ||
+        cudaMallocHost((void**)&b->errs, sizeof(int) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(-1, MR_E_NOMEM);
+    }
+    memset(b->errs, 0, sizeof(int) * n);
+    if (cudaEventRecord(b->join, b->user) != cudaSuccess) return fail(-1, MR_E_CUDA);
+    for (int i = 0; i < n; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail(i, MR_E_CUDA);
+        b->streams.push_back(st);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(i, MR_E_CUDA);
+        b->ev.push_back(e);
+        if (cudaStreamWaitEvent(st, b->join, 0) != cudaSuccess) return fail(i, MR_E_CUDA);
+        mr_solver* h = nullptr;
+        const mr_status r = mr_create(&cfgs[i], q0s[i], st, &h);
+        if (r != MR_OK) return fail(i, r);
+        h->async_err = &b->errs[i];
+        b->inst.push_back(h);
+    }
+    *out = b;
+    return MR_OK;
+}
+
+mr_status mr_batch_step(mr_batch* b, double t_target, long long* iters_out)
+{
+    if (!b) return MR_E_INVALID;
+    const int n = (int)b->inst.size();
+    for (int i = 0; i < n; ++i)
+        if (b->inst[i]->pos != 0) return batch_fail(b, i, MR_E_STATE);
+    long long it0 = 0;
+    for (mr_solver* h : b->inst) it0 += h->iters;
+    if (cudaEventRecord(b->join, b->user) != cudaSuccess) return MR_E_CUDA;
+    std::vector<int> active;
+    for (int i = 0; i < n; ++i) {
+        if (cudaStreamWaitEvent(b->streams[i], b->join, 0) != cudaSuccess) return MR_E_CUDA;
+        if (b->inst[i]->t < t_target) active.push_back(i);
+    }
+    // Each round advances every active instance by one macro step: first all
+    // CFL reductions are enqueued, then, instance by instance, the host waits
+    // for that instance's value and enqueues its macro step, while the GPU
+    // runs the macro steps already enqueued for the others.
+    while (!active.empty()) {
+        for (int i : active) {
+            mr_solver* h = b->inst[i];
+            const mr_status r = cfl_enqueue(h, &b->bits[i]);
+            if (r != MR_OK) return batch_fail(b, i, r);
+            if (cudaEventRecord(b->ev[i], h->stream) != cudaSuccess) return batch_fail(b, i, MR_E_CUDA);
+        }
+        std::vector<int> next;
+        for (int i : active) {
+            mr_solver* h = b->inst[i];
+            if (cudaEventSynchronize(b->ev[i]) != cudaSuccess) return batch_fail(b, i, MR_E_CUDA);
+            if (b->errs[i]) return batch_fail(b, i, sync_check(h));
+            const long long nit = 1LL << (h->K.g.L - h->K.g.lb);
+            double dt = cfl_from_bits(h, b->bits[i]);
+            bool last = false;
+            if (h->t + nit * dt >= t_target * (1.0 - 1e-14)) {
+                dt = (t_target - h->t) / nit;
+                last = true;
+            }
+            const double t0 = h->t;
+            const mr_status r = run_iters(h, dt, nit);
+            if (r != MR_OK) return batch_fail(b, i, r);
+            h->t = last ? t_target : t0 + nit * dt;
+            if (!last) next.push_back(i);
+        }
+        active.swap(next);
+    }
+    long long it1 = 0;
+    for (int i = 0; i < n; ++i) {
+        mr_solver* h = b->inst[i];
+        const mr_status r = sync_check(h);
+        if (r != MR_OK) return batch_fail(b, i, r);
+        if (b->errs[i]) return batch_fail(b, i, MR_E_NUMERIC);
+        it1 += h->iters;
+    }
+    if (iters_out) *iters_out = it1 - it0;
+    return MR_OK;
+}
+
+mr_solver* mr_batch_instance(mr_batch* b, int i)
+{
+    return (b && i >= 0 && i < (int)b->inst.size()) ? b->inst[i] : nullptr;
+}
+
+const char* mr_batch_last_error(const mr_batch* b) { return b ? b->err.c_str() : kNullErr; }
+
+void mr_batch_destroy(mr_batch* b)
+{
+    if (b) batch_free(b);
+}
+
+} // extern "C"

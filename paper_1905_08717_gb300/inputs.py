@@ -276,6 +276,22 @@ def rd_bumps_2d(L: int = 8, eps: float = 1e-3, seed: int = 0,
     return p, u[None, :, :].copy()
 
 
+def rd_batch(n: int = 256, seed: int = 0, levels: tuple = (7, 10), eps_choices: tuple = (1e-3, 1e-4),
+             t_end: float = 0.2) -> tuple[list, list]:
+    """n independent 2D reaction-diffusion problems of uneven size: instance i
+    has its own bumps (seed + i), finest level L ~ U{levels}, eps drawn from
+    eps_choices, RK2 with LT/NERK, Neumann walls."""
+    rng = np.random.default_rng(seed)
+    Ls = rng.integers(levels[0], levels[1] + 1, n)
+    es = rng.choice(np.asarray(eps_choices, dtype=np.float64), n)
+    probs, qs = [], []
+    for i in range(n):
+        p, q = rd_bumps_2d(L=int(Ls[i]), eps=float(es[i]), seed=seed + i, t_end=t_end)
+        probs.append(p.replace(name=f"rd2d_L{int(Ls[i])}_seed{seed + i}"))
+        qs.append(q)
+    return probs, qs
+
+
 def advection_gaussian_1d(L: int = 9, a: float = 1.0, rk_order: int = 3,
                           time_mode: int = TIME_LT,
                           t_end: float = 1.0) -> tuple[Problem, np.ndarray]:
