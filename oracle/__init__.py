@@ -35,7 +35,8 @@ class _Cfg(ctypes.Structure):
                 ("precision", ctypes.c_int), ("adapt_mode", ctypes.c_int),
                 ("reflux", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("bc", ctypes.c_int * 3), ("phys", ctypes.c_double * 8)]
+                ("bc", ctypes.c_int * 3), ("phys", ctypes.c_double * 8),
+                ("flux", ctypes.c_int)]
 
 
 _lib = None
@@ -58,6 +59,8 @@ def _load():
         _lib.or_destroy.argtypes = [vp]
         _lib.or_last_error.argtypes = [vp]
         _lib.or_last_error.restype = ctypes.c_char_p
+        _lib.or_num_flux.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     return _lib
 
 
@@ -70,7 +73,22 @@ def _cfg(p) -> _Cfg:
         c.lo[k], c.hi[k], c.bc[k] = p.lo[k], p.hi[k], p.bc[k]
     for k in range(8):
         c.phys[k] = p.phys[k]
+    c.flux = getattr(p, "flux", 0)
     return c
+
+
+def num_flux(problem, k: int, W: np.ndarray, dxf: float = 1.0) -> np.ndarray:
+    """The oracle's numerical flux across the face between cells 1 and 2 of
+    the 4-cell stencil W[4][m] (conservative values), direction k."""
+    m = problem.nvars()
+    w = np.ascontiguousarray(W, dtype=np.float64).reshape(4, m)
+    F = np.zeros(m)
+    cfg = _cfg(problem)
+    r = _load().or_num_flux(ctypes.byref(cfg), k, dxf, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if r != 0:
+        raise OracleError(f"or_num_flux: status {r}")
+    return F
 
 
 class OracleError(RuntimeError):

@@ -266,6 +266,63 @@ static double minmod(double a, double b)
     return fabs(a) < fabs(b) ? a : b;
 }
 
+/* AUSM+ flux (Liou, J. Comput. Phys. 129, 1996), the paper's flux for the
+ * Euler equations (Sec. 5), from the reconstructed primitive states PL, PR
+ * (rho, velocities, p) and conservative states UL, UR, across a face normal
+ * to direction k:
+ *   critical speed a*^2 = 2 (g-1)/(g+1) H, H = (E + p)/rho;
+ *   interface speed a = min(a*_L^2 / max(a*_L, u_L), a*_R^2 / max(a*_R, -u_R));
+ *   M_L = u_L / a, M_R = u_R / a (normal velocities);
+ *   Mach splitting M+-(M) = +-(M +- 1)^2/4 +- beta (M^2 - 1)^2 for |M| < 1,
+ *     else (M +- |M|)/2, beta = 1/8;
+ *   pressure splitting P+-(M) = (M +- 1)^2 (2 -+ M)/4 +- alpha M (M^2 - 1)^2
+ *     for |M| < 1, else (1 +- sign M)/2, alpha = 3/16;
+ *   m = M+(M_L) + M-(M_R), p_half = P+(M_L) p_L + P-(M_R) p_R;
+ *   F = a (max(m,0) Psi_L + min(m,0) Psi_R) + p_half n, Psi = rho (1, u, H). */
+static double ausm_mach(double M, int sgn)
+{
+    if (fabs(M) >= 1.0) return 0.5 * (M + sgn * fabs(M));
+    const double t = M * M - 1.0;
+    return sgn * 0.25 * (M + sgn) * (M + sgn) + sgn * 0.125 * t * t;
+}
+
+static double ausm_pres(double M, int sgn)
+{
+    if (fabs(M) >= 1.0) return M * sgn > 0.0 ? 1.0 : 0.0;
+    const double t = M * M - 1.0;
+    return 0.25 * (M + sgn) * (M + sgn) * (2.0 - sgn * M) + sgn * 0.1875 * M * t * t;
+}
+
+static void ausm_plus(double g, int d, int k, const double* PL, const double* PR, const double* UL,
+                      const double* UR, double* F)
+{
+    const int m = d + 2;
+    const double pL = PL[d + 1], pR = PR[d + 1];
+    const double HL = (UL[d + 1] + pL) / PL[0], HR = (UR[d + 1] + pR) / PR[0];
+    const double uL = PL[1 + k], uR = PR[1 + k];
+    const double asL = sqrt(2.0 * (g - 1.0) / (g + 1.0) * HL);
+    const double asR = sqrt(2.0 * (g - 1.0) / (g + 1.0) * HR);
+    const double atL = asL * asL / (asL > uL ? asL : uL);
+    const double atR = asR * asR / (asR > -uR ? asR : -uR);
+    const double a = atL < atR ? atL : atR;
+    const double ML = uL / a, MR = uR / a;
+    const double mh = ausm_mach(ML, 1) + ausm_mach(MR, -1);
+    const double ph = ausm_pres(ML, 1) * pL + ausm_pres(MR, -1) * pR;
+    const double mp = mh > 0.0 ? mh : 0.0, mm = mh < 0.0 ? mh : 0.0;
+    double psiL[MMAX], psiR[MMAX];
+    int v;
+    psiL[0] = PL[0];
+    psiR[0] = PR[0];
+    for (v = 0; v < d; v++) {
+        psiL[1 + v] = UL[1 + v];
+        psiR[1 + v] = UR[1 + v];
+    }
+    psiL[d + 1] = PL[0] * HL;
+    psiR[d + 1] = PR[0] * HR;
+    for (v = 0; v < m; v++) F[v] = a * (mp * psiL[v] + mm * psiR[v]);
+    F[1 + k] += ph;
+}
+
 /* numerical flux in direction k across the face between stencil cells 1 and 2
  * of W[0..3] (conservative values), face of width dxf. */
 static void num_flux(Orc* o, int k, double dxf, double W[4][MMAX], double* F)
@@ -331,6 +388,10 @@ static void num_flux(Orc* o, int k, double dxf, double W[4][MMAX], double* F)
     FR[1 + k] += PR[d + 1];
     FL[d + 1] += PL[d + 1] * unL;
     FR[d + 1] += PR[d + 1] * unR;
+    if (o->cfg.flux == 1) {
+        ausm_plus(g, d, k, PL, PR, UL, UR, F);
+        return;
+    }
     double cL = sqrt(g * PL[d + 1] / PL[0]), cR = sqrt(g * PR[d + 1] / PR[0]);
     double sL = unL - cL < unR - cR ? unL - cL : unR - cR;
     double sR = unL + cL > unR + cR ? unL + cL : unR + cR;
@@ -1084,7 +1145,8 @@ int or_create(const or_config* cfg, const double* q0, void** out)
         cfg->min_level < 0 || cfg->min_level > cfg->max_level || cfg->equation < 0 ||
         cfg->equation > 3 || (cfg->rk_order != 2 && cfg->rk_order != 3) ||
         cfg->precision != 0 || cfg->time_mode < 0 || cfg->time_mode > 1 ||
-        cfg->dim * cfg->max_level > 30)
+        cfg->dim * cfg->max_level > 30 || cfg->flux < 0 || cfg->flux > 1 ||
+        (cfg->flux == 1 && cfg->equation != 2))
         return OR_E_INVALID;
     Orc* o = (Orc*)calloc(1, sizeof(Orc));
     if (!o) return OR_E_NOMEM;
@@ -1396,6 +1458,25 @@ void or_destroy(void* h)
     if (!o) return;
     free_all(o);
     free(o);
+}
+
+int or_num_flux(const or_config* cfg, int k, double dxf, const double* W, double* F)
+{
+    if (!cfg || !W || !F || cfg->dim < 1 || cfg->dim > 3 || k < 0 || k >= cfg->dim || cfg->equation < 0 ||
+        cfg->equation > 3 || cfg->flux < 0 || cfg->flux > 1 || (cfg->flux == 1 && cfg->equation != 2))
+        return OR_E_INVALID;
+    Orc o;
+    memset(&o, 0, sizeof o);
+    o.cfg = *cfg;
+    o.d = cfg->dim;
+    o.m = cfg->equation == 2 ? cfg->dim + 2 : 1;
+    o.eq = cfg->equation;
+    double w[4][MMAX];
+    int i, v;
+    for (i = 0; i < 4; i++)
+        for (v = 0; v < o.m; v++) w[i][v] = W[i * o.m + v];
+    num_flux(&o, k, dxf, w, F);
+    return OR_OK;
 }
 
 const char* or_last_error(void* h)

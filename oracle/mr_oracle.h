@@ -37,6 +37,8 @@ typedef struct or_config {
     double lo[3], hi[3];/* box                                                */
     int    bc[3];       /* 0 periodic, 1 homogeneous Neumann (mirror)         */
     double phys[8];     /* advection: a_x,a_y,a_z | Euler: gamma | RD: D,k,a  */
+    int    flux;        /* 0: the equation's default flux (Euler: HLL);
+                           1: AUSM+ (Euler only), the paper's flux (Sec. 5)   */
 } or_config;
 
 enum { OR_OK = 0, OR_E_INVALID = 1, OR_E_NOMEM = 2, OR_E_STATE = 5, OR_E_NUMERIC = 6 };
@@ -58,6 +60,12 @@ int  or_iterate(void* h, double dt, long long n_iters, long long* iters_out);
 int  or_read(void* h, int what, void* buf, size_t cap_bytes, size_t* used);
 void or_destroy(void* h);
 const char* or_last_error(void* h);
+
+/* Numerical flux of the configured equation across the face between cells 1
+ * and 2 of the 4-cell stencil W (conservative values, [cell][variable]) in
+ * direction k, face width dxf: the function the solver uses, exported for
+ * tests.  Returns OR_E_INVALID for a bad configuration. */
+int or_num_flux(const or_config* cfg, int k, double dxf, const double* W, double* F);
 
 #ifdef __cplusplus
 }

@@ -33,6 +33,9 @@ ADAPT_NEVER = 0
 ADAPT_MACRO = 1
 ADAPT_EVERY = 2
 
+FLUX_DEFAULT = 0
+FLUX_AUSM_PLUS = 1
+
 PREC_FP64 = 0
 PREC_MIXED = 1   # FP32 face fluxes; state, registers and adaptation FP64
 
@@ -57,6 +60,7 @@ class Problem:
     hi: tuple = (1.0, 1.0, 1.0)
     bc: tuple = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
     phys: tuple = (0.0,) * 8
+    flux: int = 0              # 0 the equation's default flux, 1 AUSM+ (Euler)
     t_end: float = 0.0
     name: str = ""
 
@@ -86,12 +90,15 @@ def _cell_average_1d(fun, lo: float, hi: float, n: int) -> np.ndarray:
     return acc
 
 
-def _cell_average_2d(fun, lo, hi, n: int) -> np.ndarray:
-    """Tensor 4x4 Gauss-Legendre average over n x n cells, index [y, x]."""
+def _cell_average_2d(fun, lo, hi, n: int, midpoint: bool = False) -> np.ndarray:
+    """Tensor 4x4 Gauss-Legendre average over n x n cells, index [y, x]
+    (midpoint: the value at the cell centre instead)."""
     hx = (hi[0] - lo[0]) / n
     hy = (hi[1] - lo[1]) / n
     cx = lo[0] + (np.arange(n) + 0.5) * hx
     cy = lo[1] + (np.arange(n) + 0.5) * hy
+    if midpoint:
+        return fun(cx[None, :], cy[:, None])
     acc = np.zeros((n, n))
     for xg, wx in zip(_GL4_X, _GL4_W):
         for yg, wy in zip(_GL4_X, _GL4_W):
@@ -252,10 +259,11 @@ def euler_3d_blast(L: int = 8, eps: float = 1e-3, min_level: int = 3,
 def rd_bumps_2d(L: int = 8, eps: float = 1e-3, seed: int = 0,
                 min_level: int = 3, rk_order: int = 2,
                 time_mode: int = TIME_LT, D: float = 1e-3, k: float = 100.0,
-                a: float = 0.3, t_end: float = 0.2) -> tuple[Problem, np.ndarray]:
+                a: float = 0.3, t_end: float = 0.2, midpoint: bool = False) -> tuple[Problem, np.ndarray]:
     """2D bistable reaction-diffusion u_t = D lap u + k u(1-u)(u-a), Neumann,
     1..8 Gaussian bumps (centre U[.15,.85]^2, width U[.02,.06], amplitude 1),
-    combined by max; cell averages by 4x4 Gauss-Legendre."""
+    combined by max; cell averages by 4x4 Gauss-Legendre (midpoint: centre
+    values, a cheaper input for large request streams)."""
     rng = np.random.default_rng(seed)
     nb = int(rng.integers(1, 9))
     cen = rng.uniform(0.15, 0.85, (nb, 2))
@@ -267,7 +275,7 @@ def rd_bumps_2d(L: int = 8, eps: float = 1e-3, seed: int = 0,
             out = np.maximum(out, np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * w * w)))
         return out
 
-    u = _cell_average_2d(fun, (0.0, 0.0), (1.0, 1.0), 1 << L)
+    u = _cell_average_2d(fun, (0.0, 0.0), (1.0, 1.0), 1 << L, midpoint=midpoint)
     ph = (D, k, a) + (0.0,) * 5
     p = Problem(dim=2, equation=EQ_REACTION_DIFFUSION, max_level=L,
                 min_level=min_level, eps=eps, eps_mode=0, rk_order=rk_order,
@@ -290,6 +298,49 @@ def rd_batch(n: int = 256, seed: int = 0, levels: tuple = (7, 10), eps_choices: 
         probs.append(p.replace(name=f"rd2d_L{int(Ls[i])}_seed{seed + i}"))
         qs.append(q)
     return probs, qs
+
+
+def serving_requests(n: int = 300, seed: int = 0, rate: float = 200.0) -> list:
+    """A seeded stream of n requests arriving as a Poisson process of the given
+    rate (per second): (arrival_s, problem, q0, t_end).  Kinds, equally
+    likely: 1D Burgers (L ~ U{10..14}), 2D reaction-diffusion (L ~ U{8..10}),
+    3D Euler blast (L ~ U{6..8}); eps ~ log-uniform [1e-4, 1e-2]; mixed
+    precision; the coarsest level keeps a macro step at 2^7 fine steps or
+    fewer.  t_end is set from a target of fine iterations at the initial CFL
+    step, so that request sizes stay bounded."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    cache = {}  # Burgers and blast data depend on L only
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        kind = int(rng.integers(0, 3))
+        eps = float(10.0 ** rng.uniform(-4.0, -2.0))
+        if kind == 0:
+            L = int(rng.integers(10, 15))
+            if ("b", L) not in cache:
+                cache[("b", L)] = burgers_1d(L=L, eps=eps, min_level=L - 7)
+            p, q = cache[("b", L)]
+            p = p.replace(eps=eps)
+            its = int(rng.integers(128, 513))
+            t_end = its * 0.5 / (1 << L)            # speed max |u| = 1
+        elif kind == 1:
+            L = int(rng.integers(8, 11))
+            p, q = rd_bumps_2d(L=L, eps=eps, seed=seed + i, rk_order=2, midpoint=True)
+            its = int(rng.integers(64, 257))
+            dx = 1.0 / (1 << L)
+            t_end = its * 0.5 * dx * dx / (4.0 * p.phys[0])  # diffusion limit
+        else:
+            L = int(rng.integers(6, 9))
+            if ("e", L) not in cache:
+                cache[("e", L)] = euler_3d_blast(L=L, eps=eps, min_level=L - 4)
+            p, q = cache[("e", L)]
+            p = p.replace(eps=eps)
+            its = int(rng.integers(32, 97))
+            t_end = its * 0.5 / (1 << L) / 4.0      # speed ~ 3.74
+        p = p.replace(precision=PREC_MIXED, name=f"req{i}_{p.name}")
+        out.append((t, p, q, float(t_end)))
+    return out
 
 
 def advection_gaussian_1d(L: int = 9, a: float = 1.0, rk_order: int = 3,

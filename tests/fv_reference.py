@@ -74,3 +74,70 @@ def poly_cell_average(coeffs, a, b):
     for k, ck in enumerate(coeffs):
         out = out + ck * (b ** (k + 1) - a ** (k + 1)) / ((k + 1) * (b - a))
     return out
+
+
+def exact_riemann(left, right, gamma, xi):
+    """Exact solution of the 1D Euler Riemann problem with states
+    left = (rho, u, p), right = (rho, u, p), sampled at the similarity
+    coordinates xi = (x - x0) / t.  Returns rho, u, p arrays.  The star
+    pressure solves f_L(p) + f_R(p) + u_R - u_L = 0 (shock branch: Rankine-
+    Hugoniot, rarefaction branch: isentropic), by Newton iteration from the
+    two-rarefaction estimate; the waves are then sampled."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    g = gamma
+    cl, cr = np.sqrt(g * pl / rl), np.sqrt(g * pr / rr)
+
+    def f(p, rk, pk, ck):
+        if p > pk:  # shock
+            A, B = 2.0 / ((g + 1.0) * rk), (g - 1.0) / (g + 1.0) * pk
+            s = np.sqrt(A / (p + B))
+            return (p - pk) * s, s * (1.0 - 0.5 * (p - pk) / (p + B))
+        r = (p / pk) ** ((g - 1.0) / (2.0 * g))
+        return 2.0 * ck / (g - 1.0) * (r - 1.0), 1.0 / (rk * ck) * (p / pk) ** (-(g + 1.0) / (2.0 * g))
+
+    z = (g - 1.0) / (2.0 * g)
+    p = ((cl + cr - 0.5 * (g - 1.0) * (ur - ul)) / (cl / pl ** z + cr / pr ** z)) ** (1.0 / z)
+    for _ in range(100):
+        fl, dl = f(p, rl, pl, cl)
+        fr, dr = f(p, rr, pr, cr)
+        dp = (fl + fr + ur - ul) / (dl + dr)
+        p = max(p - dp, 1e-14)
+        if abs(dp) < 1e-15 * p:
+            break
+    fl, _ = f(p, rl, pl, cl)
+    fr, _ = f(p, rr, pr, cr)
+    us = 0.5 * (ul + ur) + 0.5 * (fr - fl)
+    gm = (g - 1.0) / (g + 1.0)
+    out_r, out_u, out_p = np.empty_like(xi), np.empty_like(xi), np.empty_like(xi)
+    for i, s in enumerate(np.asarray(xi, dtype=float)):
+        if s <= us:  # left of the contact
+            if p > pl:
+                sl = ul - cl * np.sqrt((g + 1.0) / (2.0 * g) * p / pl + (g - 1.0) / (2.0 * g))
+                v = (rl, ul, pl) if s <= sl else (rl * (p / pl + gm) / (gm * p / pl + 1.0), us, p)
+            else:
+                csl = cl * (p / pl) ** z
+                if s <= ul - cl:
+                    v = (rl, ul, pl)
+                elif s >= us - csl:
+                    v = (rl * (p / pl) ** (1.0 / g), us, p)
+                else:
+                    c = 2.0 / (g + 1.0) * (cl + 0.5 * (g - 1.0) * (ul - s))
+                    uu = 2.0 / (g + 1.0) * (cl + 0.5 * (g - 1.0) * ul + s)
+                    v = (rl * (c / cl) ** (2.0 / (g - 1.0)), uu, pl * (c / cl) ** (2.0 * g / (g - 1.0)))
+        else:  # right of the contact
+            if p > pr:
+                sr = ur + cr * np.sqrt((g + 1.0) / (2.0 * g) * p / pr + (g - 1.0) / (2.0 * g))
+                v = (rr, ur, pr) if s >= sr else (rr * (p / pr + gm) / (gm * p / pr + 1.0), us, p)
+            else:
+                csr = cr * (p / pr) ** z
+                if s >= ur + cr:
+                    v = (rr, ur, pr)
+                elif s <= us + csr:
+                    v = (rr * (p / pr) ** (1.0 / g), us, p)
+                else:
+                    c = 2.0 / (g + 1.0) * (cr - 0.5 * (g - 1.0) * (ur - s))
+                    uu = 2.0 / (g + 1.0) * (-cr + 0.5 * (g - 1.0) * ur + s)
+                    v = (rr * (c / cr) ** (2.0 / (g - 1.0)), uu, pr * (c / cr) ** (2.0 * g / (g - 1.0)))
+        out_r[i], out_u[i], out_p[i] = v
+    return out_r, out_u, out_p
