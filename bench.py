@@ -22,6 +22,11 @@ import sys
 import tempfile
 import time
 
+# 32 hardware work queues instead of the default 8, so that the batched and
+# served instances (one stream each) run concurrently; must be set before
+# the CUDA context exists, and does not affect single-stream work
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -47,6 +52,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--t-end", type=float, default=T_END)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-instances and serving measurements")
     ap.add_argument("--profile-run", action="store_true",
                     help="only the timed LT solves (no e2e / GTS / peaks); for ncu captures")
     ap.add_argument("--level", type=int, default=10, help="finest level (profiling runs)")
@@ -139,6 +146,92 @@ def _traffic_per_leaf_stage():
             except ValueError:
                 return None
     return None
+
+
+def _batched(pkg, inputs, torch, n: int = 256, t1: float = 0.005, span: float = 0.02) -> dict:
+    """Batched instances: n 2D reaction-diffusion problems of uneven size (L
+    ~ U{7..10}, eps in {1e-3, 1e-4}, RK2 LT/NERK) advanced from t1 to
+    t1 + span in one mr_batch_step, against the same instances solved one
+    after another over the same span (host wall clock, both synchronised)."""
+    probs, qs = inputs.rd_batch(n=n, seed=0, t_end=0.2)
+    b = pkg.Batch(probs, qs)
+    b.step(t1)  # captures every instance's macro-step graph
+    u0 = sum(v.stats()["updates"] for v in b.instances)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(t1 + span)
+    t_batch = time.perf_counter() - t0
+    u1 = sum(v.stats()["updates"] for v in b.instances)
+    b.close()
+    t_seq = 0.0
+    for p, q in zip(probs, qs):
+        s = pkg.Solver(p, q)
+        s.step(t1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(t1 + span)
+        t_seq += time.perf_counter() - t0
+        s.close()
+    return {"workload": f"rd2d x{n}, L~U{{7..10}}, eps in {{1e-3,1e-4}}, rk2 lt/nerk, t {t1}->{t1 + span}",
+            "leaf_updates": u1 - u0, "batch_s": t_batch, "updates_per_s": (u1 - u0) / t_batch,
+            "one_by_one_s": t_seq, "one_by_one_updates_per_s": (u1 - u0) / t_seq,
+            "speedup": t_seq / t_batch, "timing": "host wall clock around synchronous calls"}
+
+
+def _serve(pkg, torch, reqs) -> dict:
+    """Replay (arrival_s, problem, q0, t_end) requests against a fresh
+    mr_server in real time (host clock); latency = completion seen by poll -
+    arrival."""
+    n = len(reqs)
+    srv = pkg.Server(mem_budget_bytes=64 << 30, max_active=96)
+    arrival, done_at, updates = {}, {}, 0
+    k = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while len(done_at) < n:
+        now = time.perf_counter() - t0
+        while k < n and reqs[k][0] <= now:
+            a, p, q, t_end = reqs[k]
+            arrival[srv.submit(p, q, t_end)] = a
+            k += 1
+        active, queued = srv.advance()
+        got = srv.poll()
+        for rid in got:
+            done_at[rid] = time.perf_counter() - t0
+            if srv.status(rid) != 0:
+                raise RuntimeError(f"request {rid} failed")
+            updates += srv.result(rid).stats()["updates"]
+            srv.release(rid)
+        if active == 0 and queued == 0 and k < n:
+            time.sleep(max(0.0, reqs[k][0] - (time.perf_counter() - t0)))
+        elif not got:
+            time.sleep(5e-5)  # advance() never waits: pause briefly between polls
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = sorted(1e3 * (done_at[r] - arrival[r]) for r in done_at)
+    return {"latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": lat[-1]},
+            "requests_per_s": n / wall, "leaf_updates_per_s": updates / wall, "wall_s": wall}
+
+
+def _serving(pkg, inputs, torch, n: int = 200, rate: float = 200.0) -> dict:
+    """Continuous batching on the request mix of a Poisson stream: first the
+    capacity (every request submitted at t = 0), then latency with the same
+    requests arriving as a Poisson process at half that capacity, then at the
+    configured rate when the GPU can sustain it."""
+    reqs = inputs.serving_requests(n=n, seed=0, rate=rate)
+    sat = _serve(pkg, torch, [(0.0,) + r[1:] for r in reqs])
+    cap = sat["requests_per_s"]
+    rng = __import__("numpy").random.default_rng(1)
+    arr = list(__import__("itertools").accumulate(rng.exponential(1.0 / (0.5 * cap), n)))
+    half = _serve(pkg, torch, [(a,) + r[1:] for a, r in zip(arr, reqs)])
+    out = {"workload": f"{n} requests: 1D Burgers L10-14 (32-128 fine steps), 2D RD L8-10 (16-64), "
+                       "3D blast L6-8 (8-24); eps log-U[1e-4,1e-2]; mixed precision",
+           "capacity": sat, "at_half_capacity": dict(half, rate_per_s=0.5 * cap),
+           "configured_rate_per_s": rate, "timing": "host wall clock"}
+    if rate <= cap:
+        out["at_configured_rate"] = _serve(pkg, torch, reqs)
+    return out
 
 
 def _cpu_baseline(seconds: float = 12.0) -> dict:
@@ -365,6 +458,9 @@ def run_ours(args):
              "rel_l1_vs_fp64": [float(x) for x in rel_l1],
              "arithmetic": "FP32 reconstruction + face fluxes; FP64 state, RK update, registers, adaptation"}
 
+    batched = _batched(pkg, inputs, torch) if not args.no_batch else None
+    serving = _serving(pkg, inputs, torch) if not args.no_batch else None
+
     lat_ms = sorted(1e3 * x for x in lat)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
@@ -383,6 +479,10 @@ def run_ours(args):
                    "updates_per_s": gst["updates"] / gts_s},
            "lt_speedup_vs_gts": gts_s / (tmax / args.steps),
            "precision_mode": mixed}
+    if batched is not None:
+        out["batched"] = batched
+    if serving is not None:
+        out["serving"] = serving
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = _cpu_baseline()
     print(json.dumps(out), flush=True)

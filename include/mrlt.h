@@ -55,6 +55,10 @@ enum { MR_ADAPT_NEVER = 0, MR_ADAPT_MACRO = 1, MR_ADAPT_EVERY = 2 };
  * averages, the RK updates, the flux registers, the CFL reduction and the whole
  * adaptation (details, thresholds, prediction, projection) stay FP64. */
 enum { MR_PREC_FP64 = 0, MR_PREC_MIXED = 1 };
+/* Numerical flux.  MR_FLUX_AUSM_PLUS (Euler only) is the advection upstream
+ * splitting of Liou (1996), the flux the paper uses for its Euler cases
+ * (Sec. 5); the default for Euler is HLL. */
+enum { MR_FLUX_DEFAULT = 0, MR_FLUX_AUSM_PLUS = 1 };
 
 /* Problem statement (Sec. 2, Eq. 1) and the method's parameters. */
 typedef struct mr_config {
@@ -77,6 +81,7 @@ typedef struct mr_config {
     double lo[3], hi[3];/* box [lo, hi] per direction (unused entries ignored)      */
     int    bc[3];      /* MR_BC_* per direction                                     */
     double phys[8];    /* advection: a_x, a_y, a_z | Euler: gamma | RD: D, k, a     */
+    int    flux;       /* MR_FLUX_DEFAULT (Euler: HLL) or MR_FLUX_AUSM_PLUS (Euler)  */
 } mr_config;
 
 /* Create a solver from the finest-level cell averages q0 (host, float64, layout
@@ -200,7 +205,9 @@ mr_status mr_batch_create(int n, const mr_config* cfgs, const double* const* q0s
                           mr_batch** out, int* failed_index);
 
 /* Advance every instance to t_target as mr_step does (whole macro steps of its
- * own CFL step, the last shortened), all instances concurrently.  Every
+ * own CFL step, the last shortened), all instances concurrently, each at the
+ * pace of its own stream (the host queues an instance's next macro step as
+ * soon as its CFL value has arrived).  Every
  * instance must be at a macro-step boundary.  *iters_out (may be NULL)
  * receives the fine iterations done, summed over instances.  On an error the
  * failing instance is reported by mr_batch_last_error. */
@@ -216,6 +223,58 @@ const char* mr_batch_last_error(const mr_batch* b);
 
 /* Release the batch and all its instances (NULL is ignored). */
 void mr_batch_destroy(mr_batch* b);
+
+/* ---- Serving -------------------------------------------------------------
+ * Problems that arrive over time, each with its own end time, served by
+ * continuous batching: every admitted problem advances by whole macro steps
+ * at the pace of its own stream (as in mr_batch_step); queued problems join
+ * at macro-step boundaries, first come first served, while their
+ * device footprint fits the memory budget and fewer than max_active problems
+ * are in flight; a problem leaves when it reaches its end time.  The paper has
+ * no counterpart.  The footprint of a configuration is known before it is
+ * created (the level grids are dense): the exact bytes the solver will
+ * allocate.  Results stay on the device until released. */
+typedef struct mr_server mr_server;
+
+/* mem_budget_bytes: device bytes all admitted problems may hold together;
+ * max_active >= 1: problems in flight at once.  Work is ordered after the
+ * work on cuda_stream at creation. */
+mr_status mr_server_create(size_t mem_budget_bytes, int max_active, void* cuda_stream, mr_server** out);
+
+/* Queue a problem (cfg and finest data q0 as for mr_create; q0 is copied) to
+ * be advanced from t = 0 to t_end.  *id receives its request id.  MR_E_NOMEM
+ * if the problem alone exceeds the budget, MR_E_INVALID for a bad config. */
+mr_status mr_server_submit(mr_server* s, const mr_config* cfg, const double* q0, double t_end, long long* id);
+
+/* Admit what fits, then queue the next macro step of every active problem
+ * whose previous one has completed.  Never waits for the GPU: call it in a
+ * loop.  *n_active (problems admitted and not yet reported) and *n_queued
+ * may be NULL. */
+mr_status mr_server_advance(mr_server* s, int* n_active, int* n_queued);
+
+/* Ids of up to cap problems that finished since the last poll (in the order
+ * they were found finished); *n_done receives how many were written. */
+mr_status mr_server_poll(mr_server* s, long long* ids, int cap, int* n_done);
+
+/* Outcome of a finished request (MR_E_STATE while it is not finished,
+ * MR_E_INVALID for an unknown id). */
+mr_status mr_server_status(mr_server* s, long long id);
+
+/* The solver of a finished request, for mr_read; NULL otherwise.  Owned by the
+ * server until mr_server_release. */
+mr_solver* mr_server_result(mr_server* s, long long id);
+
+/* Free a finished request and its device memory. */
+mr_status mr_server_release(mr_server* s, long long id);
+
+/* Device bytes held by admitted, not yet released requests. */
+size_t mr_server_memory(const mr_server* s);
+
+/* Reason for the last failure of a server call. */
+const char* mr_server_last_error(const mr_server* s);
+
+/* Release the server and every request it holds (NULL is ignored). */
+void mr_server_destroy(mr_server* s);
 
 #ifdef __cplusplus
 }

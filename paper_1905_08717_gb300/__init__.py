@@ -36,7 +36,8 @@ class mr_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("adapt_mode", ctypes.c_int),
                 ("reflux", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("bc", ctypes.c_int * 3), ("phys", ctypes.c_double * 8)]
+                ("bc", ctypes.c_int * 3), ("phys", ctypes.c_double * 8),
+                ("flux", ctypes.c_int)]
 
 
 _lib = None
@@ -78,9 +79,24 @@ def library() -> ctypes.CDLL:
         lib.mr_batch_last_error.argtypes = [vp]
         lib.mr_batch_last_error.restype = ctypes.c_char_p
         lib.mr_batch_destroy.argtypes = [vp]
+        lib.mr_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, vp, ctypes.POINTER(vp)]
+        lib.mr_server_submit.argtypes = [vp, ctypes.POINTER(mr_config), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_double, ctypes.POINTER(ll)]
+        lib.mr_server_advance.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        lib.mr_server_poll.argtypes = [vp, ctypes.POINTER(ll), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.mr_server_status.argtypes = [vp, ll]
+        lib.mr_server_result.argtypes = [vp, ll]
+        lib.mr_server_result.restype = vp
+        lib.mr_server_release.argtypes = [vp, ll]
+        lib.mr_server_memory.argtypes = [vp]
+        lib.mr_server_memory.restype = ctypes.c_size_t
+        lib.mr_server_last_error.argtypes = [vp]
+        lib.mr_server_last_error.restype = ctypes.c_char_p
+        lib.mr_server_destroy.argtypes = [vp]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
                      "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create",
-                     "mr_batch_step"):
+                     "mr_batch_step", "mr_server_create", "mr_server_submit", "mr_server_advance",
+                     "mr_server_poll", "mr_server_status", "mr_server_release"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -95,6 +111,7 @@ def make_config(p) -> mr_config:
         c.lo[k], c.hi[k], c.bc[k] = p.lo[k], p.hi[k], p.bc[k]
     for k in range(8):
         c.phys[k] = p.phys[k]
+    c.flux = getattr(p, "flux", 0)
     return c
 
 
@@ -273,6 +290,73 @@ class Batch:
                 v._h = ctypes.c_void_p()
             library().mr_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (C-ABI `mr_server`): problems are
+    submitted with their own end time, join the running set at round
+    boundaries while their device footprint fits the budget, and are
+    reported by poll() when finished."""
+
+    def __init__(self, mem_budget_bytes: int, max_active: int, stream=None):
+        lib = library()
+        self._s = ctypes.c_void_p()
+        r = lib.mr_server_create(int(mem_budget_bytes), int(max_active),
+                                 ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(self._s))
+        if r != 0:
+            raise MRError(r, "mr_server_create failed")
+        self._problems = {}
+
+    def _check(self, r: int, what: str):
+        if r != 0:
+            raise MRError(r, f"{what}: {library().mr_server_last_error(self._s).decode()}")
+
+    def submit(self, problem, q0, t_end: float) -> int:
+        cfg = make_config(problem)
+        q = np.ascontiguousarray(q0, dtype=np.float64).reshape(problem.nvars(), -1)
+        rid = ctypes.c_longlong()
+        self._check(library().mr_server_submit(self._s, ctypes.byref(cfg), _dptr(q), float(t_end),
+                                               ctypes.byref(rid)), "submit")
+        self._problems[rid.value] = problem
+        return rid.value
+
+    def advance(self):
+        a, qd = ctypes.c_int(), ctypes.c_int()
+        self._check(library().mr_server_advance(self._s, ctypes.byref(a), ctypes.byref(qd)), "advance")
+        return a.value, qd.value
+
+    def poll(self, cap: int = 4096) -> list:
+        ids = (ctypes.c_longlong * cap)()
+        n = ctypes.c_int()
+        self._check(library().mr_server_poll(self._s, ids, cap, ctypes.byref(n)), "poll")
+        return [ids[i] for i in range(n.value)]
+
+    def status(self, rid: int) -> int:
+        return library().mr_server_status(self._s, rid)
+
+    def result(self, rid: int) -> "Solver":
+        h = library().mr_server_result(self._s, rid)
+        if not h:
+            raise MRError(5, f"request {rid} is not finished")
+        return Solver._view(self._problems[rid], h, self)
+
+    def release(self, rid: int):
+        self._check(library().mr_server_release(self._s, rid), "release")
+        self._problems.pop(rid, None)
+
+    def memory(self) -> int:
+        return int(library().mr_server_memory(self._s))
+
+    def close(self):
+        if getattr(self, "_s", None):
+            library().mr_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:

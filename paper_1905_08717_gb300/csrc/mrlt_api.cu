@@ -10,6 +10,8 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <chrono>
+#include <thread>
 
 using namespace mrlt;
 
@@ -47,6 +49,10 @@ struct mr_solver {
     // batched use: the macro-step finiteness check copies the device error
     // bits here (pinned host memory) instead of synchronising
     int* async_err = nullptr;
+    // device bytes requested by dev_alloc; with dry set nothing is allocated
+    // (the footprint of a configuration is projected without creating it)
+    size_t bytes = 0;
+    bool dry = false;
 };
 
 namespace {
@@ -78,6 +84,8 @@ mr_status validate(const mr_config* c)
     if (c->rk_order != 2 && c->rk_order != 3) return MR_E_INVALID;
     if (c->time_mode != MR_TIME_GTS && c->time_mode != MR_TIME_LT_NERK) return MR_E_INVALID;
     if (c->precision != MR_PREC_FP64 && c->precision != MR_PREC_MIXED) return MR_E_INVALID;
+    if (c->flux != MR_FLUX_DEFAULT && !(c->flux == MR_FLUX_AUSM_PLUS && c->equation == MR_EQ_EULER))
+        return MR_E_INVALID;
     if (c->adapt_mode < 0 || c->adapt_mode > 2) return MR_E_INVALID;
     if (!(c->cfl > 0.0) || !(c->eps >= 0.0)) return MR_E_INVALID;
     for (int k = 0; k < c->dim; ++k) {
@@ -93,6 +101,8 @@ mr_status dev_alloc(mr_solver* h, T** p, size_t count)
 {
     *p = nullptr;
     if (count == 0) return MR_OK;
+    h->bytes += (count * sizeof(T) + 255) / 256 * 256;
+    if (h->dry) return MR_OK;
     cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
     if (e != cudaSuccess) {
         h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -408,16 +418,14 @@ mr_status init_state(mr_solver* h, const double* q0)
 
 extern "C" {
 
-mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, mr_solver** out)
+} // extern "C"
+
+namespace {
+
+// Grid layout of a configuration and the device allocations of a solver
+// (counted only, when h->dry is set).
+mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
 {
-    if (!out) return MR_E_INVALID;
-    *out = nullptr;
-    if (validate(cfg) != MR_OK || !q0) return MR_E_INVALID;
-    mr_solver* h = new (std::nothrow) mr_solver();
-    if (!h) return MR_E_NOMEM;
-    h->cfg = *cfg;
-    h->stream = (cudaStream_t)cuda_stream;
-    h->K.st = h->stream;
     Grid& g = h->K.g;
     memset(&g, 0, sizeof g);
     g.d = cfg->dim;
@@ -433,6 +441,7 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     g.eps = cfg->eps;
     g.eps_mode = cfg->eps_mode;
     g.prec = cfg->precision;
+    g.flux = cfg->flux;
     long long off = 0, toff = 0;
     for (int l = g.lb; l <= g.L; ++l) {
         g.toff[l] = toff;
@@ -478,7 +487,7 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     A(dev_alloc(h, &g.wmax, 1));
     A(dev_alloc(h, &g.updates, 1));
     A(dev_alloc(h, &g.work, (LMAX + 1) * 4));
-    if (r == MR_OK && cudaMemset(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long)) != cudaSuccess)
+    if (r == MR_OK && !h->dry && cudaMemset(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long)) != cudaSuccess)
         r = MR_E_CUDA; // cumulative counters: never cleared by mr_reset
     long long nblk = 0;
     for (int l = g.lb; l <= g.L; ++l) nblk += (g.N[l] + NTHREADS - 1) / NTHREADS;
@@ -487,6 +496,24 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     A(dev_alloc(h, &h->d_T, nd));
     A(dev_alloc(h, &h->d_us, off));
     A(dev_alloc(h, &h->d_keys, off * 4));
+    return r;
+}
+
+} // namespace
+
+extern "C" {
+
+mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, mr_solver** out)
+{
+    if (!out) return MR_E_INVALID;
+    *out = nullptr;
+    if (validate(cfg) != MR_OK || !q0) return MR_E_INVALID;
+    mr_solver* h = new (std::nothrow) mr_solver();
+    if (!h) return MR_E_NOMEM;
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->K.st = h->stream;
+    mr_status r = layout_alloc(h, cfg);
     if (r == MR_OK) r = init_state(h, q0);
     if (r != MR_OK) {
         fprintf(stderr, "mr_create: %s\n", h->err.c_str());
@@ -757,6 +784,78 @@ long long mr_launch_count(const mr_solver* h) { return h ? h->K.n + h->stage_lau
 
 } // extern "C"
 
+// ---------------------------------------------------------------- progress
+// Non-blocking progress of one problem toward t_target by whole macro steps.
+// The CFL reduction of the next macro step is queued behind the current one,
+// on the problem's own stream, with its value landing in *bits and an event
+// recorded after it; once the event has fired, the host picks the step, the
+// macro step (a graph) and the next CFL reduction are queued, and so on.  No
+// call waits, so every problem runs at the pace of its own stream.
+namespace {
+
+enum { PG_IDLE = 0, PG_WAIT = 1, PG_DONE = 2 };
+
+struct Progress {
+    int phase = PG_IDLE;
+    mr_status status = MR_OK;
+};
+
+// queue the CFL reduction of the next macro step
+mr_status progress_start(mr_solver* h, unsigned long long* bits, cudaEvent_t ev, Progress* pg)
+{
+    MR_TRY(cfl_enqueue(h, bits));
+    MR_CK(cudaEventRecord(ev, h->stream));
+    pg->phase = PG_WAIT;
+    return MR_OK;
+}
+
+// one non-blocking attempt; returns true when the problem made progress
+bool progress_poll(mr_solver* h, double t_target, unsigned long long* bits, const int* err, cudaEvent_t ev,
+                   Progress* pg)
+{
+    if (pg->phase == PG_DONE) return false;
+    if (pg->phase == PG_IDLE) {
+        pg->status = progress_start(h, bits, ev, pg);
+        if (pg->status != MR_OK) pg->phase = PG_DONE;
+        return true;
+    }
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaErrorNotReady) return false;
+    pg->phase = PG_DONE;
+    if (e != cudaSuccess) {
+        pg->status = MR_E_CUDA;
+        return true;
+    }
+    if (*err) { // the finiteness check of the previous macro step failed
+        pg->status = sync_check(h);
+        if (pg->status == MR_OK) pg->status = MR_E_NUMERIC;
+        return true;
+    }
+    const long long nit = 1LL << (h->K.g.L - h->K.g.lb);
+    double dt = cfl_from_bits(h, *bits);
+    bool last = false;
+    if (h->t + nit * dt >= t_target * (1.0 - 1e-14)) {
+        dt = (t_target - h->t) / nit;
+        last = true;
+    }
+    const double t0 = h->t;
+    pg->status = run_iters(h, dt, nit);
+    h->t = last ? t_target : t0 + nit * dt;
+    if (pg->status == MR_OK && !last) {
+        pg->status = progress_start(h, bits, ev, pg);
+        if (pg->status != MR_OK) pg->phase = PG_DONE;
+    }
+    return true;
+}
+
+// brief host pause when no problem could progress
+void progress_pause()
+{
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+}
+
+} // namespace
+
 // ---------------------------------------------------------------- batches
 struct mr_batch {
     std::vector<mr_solver*> inst;
@@ -849,36 +948,20 @@ mr_status mr_batch_step(mr_batch* b, double t_target, long long* iters_out)
         if (cudaStreamWaitEvent(b->streams[i], b->join, 0) != cudaSuccess) return MR_E_CUDA;
         if (b->inst[i]->t < t_target) active.push_back(i);
     }
-    // Each round advances every active instance by one macro step: first all
-    // CFL reductions are enqueued, then, instance by instance, the host waits
-    // for that instance's value and enqueues its macro step, while the GPU
-    // runs the macro steps already enqueued for the others.
-    while (!active.empty()) {
+    // every instance progresses at its own pace (see progress_poll)
+    std::vector<Progress> pg(n);
+    for (int i = 0; i < n; ++i)
+        if (b->inst[i]->t >= t_target) pg[i].phase = PG_DONE;
+    for (;;) {
+        bool busy = false, moved = false;
         for (int i : active) {
-            mr_solver* h = b->inst[i];
-            const mr_status r = cfl_enqueue(h, &b->bits[i]);
-            if (r != MR_OK) return batch_fail(b, i, r);
-            if (cudaEventRecord(b->ev[i], h->stream) != cudaSuccess) return batch_fail(b, i, MR_E_CUDA);
+            if (pg[i].phase == PG_DONE) continue;
+            moved |= progress_poll(b->inst[i], t_target, &b->bits[i], &b->errs[i], b->ev[i], &pg[i]);
+            if (pg[i].phase == PG_DONE && pg[i].status != MR_OK) return batch_fail(b, i, pg[i].status);
+            busy |= pg[i].phase != PG_DONE;
         }
-        std::vector<int> next;
-        for (int i : active) {
-            mr_solver* h = b->inst[i];
-            if (cudaEventSynchronize(b->ev[i]) != cudaSuccess) return batch_fail(b, i, MR_E_CUDA);
-            if (b->errs[i]) return batch_fail(b, i, sync_check(h));
-            const long long nit = 1LL << (h->K.g.L - h->K.g.lb);
-            double dt = cfl_from_bits(h, b->bits[i]);
-            bool last = false;
-            if (h->t + nit * dt >= t_target * (1.0 - 1e-14)) {
-                dt = (t_target - h->t) / nit;
-                last = true;
-            }
-            const double t0 = h->t;
-            const mr_status r = run_iters(h, dt, nit);
-            if (r != MR_OK) return batch_fail(b, i, r);
-            h->t = last ? t_target : t0 + nit * dt;
-            if (!last) next.push_back(i);
-        }
-        active.swap(next);
+        if (!busy) break;
+        if (!moved) progress_pause();
     }
     long long it1 = 0;
     for (int i = 0; i < n; ++i) {
@@ -902,6 +985,268 @@ const char* mr_batch_last_error(const mr_batch* b) { return b ? b->err.c_str() :
 void mr_batch_destroy(mr_batch* b)
 {
     if (b) batch_free(b);
+}
+
+} // extern "C"
+
+// ---------------------------------------------------------------- serving
+// A request: one problem with its own end time.  State: queued -> active
+// (admitted, advancing one macro step per round) -> finishing (last macro
+// step enqueued) -> done (its stream reached the end; result readable).
+struct mr_request {
+    long long id = 0;
+    mr_config cfg{};
+    std::vector<double> q0;
+    double t_end = 0.0;
+    size_t bytes = 0;       // projected device footprint
+    int slot = -1;          // pinned host slot while admitted
+    mr_solver* h = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;   // CFL value has arrived
+    cudaEvent_t fin = nullptr;  // all work of the request has completed
+    int state = 0;              // 0 queued, 1 active, 2 finishing, 3 done
+    mr_status status = MR_OK;
+    Progress pg;
+};
+
+struct mr_server {
+    size_t budget = 0, used = 0;
+    int max_active = 0;
+    cudaStream_t user = nullptr;
+    long long next_id = 1;
+    std::vector<mr_request*> queue, active, finishing;
+    std::vector<long long> completed;  // finished, not yet reported by poll
+    std::vector<mr_request*> all;      // every request not yet released
+    unsigned long long* bits = nullptr; // pinned [max_active]
+    int* errs = nullptr;                // pinned [max_active]
+    std::vector<int> free_slots;
+    std::string err;
+};
+
+namespace {
+
+void request_free(mr_server* s, mr_request* q)
+{
+    if (q->h) mr_destroy(q->h);
+    if (q->ev) cudaEventDestroy(q->ev);
+    if (q->fin) cudaEventDestroy(q->fin);
+    if (q->st) cudaStreamDestroy(q->st);
+    if (q->slot >= 0) s->free_slots.push_back(q->slot);
+    if (q->state == 1 || q->state == 2 || (q->state == 3 && q->h)) s->used -= q->bytes;
+    delete q;
+}
+
+mr_request* find_request(mr_server* s, long long id)
+{
+    for (mr_request* q : s->all)
+        if (q->id == id) return q;
+    return nullptr;
+}
+
+// projected device bytes of a configuration (the solver's allocations)
+size_t projected_bytes(const mr_config* cfg)
+{
+    mr_solver probe;
+    probe.dry = true;
+    probe.cfg = *cfg;
+    layout_alloc(&probe, cfg);
+    return probe.bytes;
+}
+
+// admit queued requests in arrival order while the budget and the slot
+// count allow; a request that fails to start is completed with its status
+mr_status admit(mr_server* s)
+{
+    size_t k = 0;
+    while (k < s->queue.size()) {
+        mr_request* q = s->queue[k];
+        if ((int)s->active.size() + (int)s->finishing.size() >= s->max_active || s->free_slots.empty() ||
+            s->used + q->bytes > s->budget)
+            break; // first come, first served: later requests wait too
+        q->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        s->errs[q->slot] = 0;
+        mr_status r = MR_OK;
+        if (cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&q->fin, cudaEventDisableTiming) != cudaSuccess)
+            r = MR_E_CUDA;
+        if (r == MR_OK) r = mr_create(&q->cfg, q->q0.data(), q->st, &q->h);
+        q->q0.clear();
+        q->q0.shrink_to_fit();
+        ++k;
+        if (r != MR_OK) {
+            s->free_slots.push_back(q->slot);
+            q->slot = -1;
+            q->status = r;
+            q->state = 3;
+            s->completed.push_back(q->id);
+            continue;
+        }
+        q->h->async_err = &s->errs[q->slot];
+        s->used += q->bytes;
+        q->state = q->h->t < q->t_end ? 1 : 2;
+        if (q->state == 1) s->active.push_back(q);
+        else {
+            cudaEventRecord(q->fin, q->st);
+            s->finishing.push_back(q);
+        }
+    }
+    s->queue.erase(s->queue.begin(), s->queue.begin() + k);
+    return MR_OK;
+}
+
+// move finished requests whose stream has drained to the completed list
+void reap(mr_server* s)
+{
+    std::vector<mr_request*> keep;
+    for (mr_request* q : s->finishing) {
+        const cudaError_t e = cudaEventQuery(q->fin);
+        if (e == cudaErrorNotReady) {
+            keep.push_back(q);
+            continue;
+        }
+        if (q->status == MR_OK) q->status = e != cudaSuccess ? MR_E_CUDA : sync_check(q->h);
+        if (q->status == MR_OK && s->errs[q->slot]) q->status = MR_E_NUMERIC;
+        s->free_slots.push_back(q->slot);
+        q->slot = -1;
+        q->state = 3;
+        s->completed.push_back(q->id);
+    }
+    s->finishing.swap(keep);
+}
+
+} // namespace
+
+extern "C" {
+
+mr_status mr_server_create(size_t mem_budget_bytes, int max_active, void* cuda_stream, mr_server** out)
+{
+    if (!out) return MR_E_INVALID;
+    *out = nullptr;
+    if (max_active < 1 || mem_budget_bytes == 0) return MR_E_INVALID;
+    mr_server* s = new (std::nothrow) mr_server();
+    if (!s) return MR_E_NOMEM;
+    s->budget = mem_budget_bytes;
+    s->max_active = max_active;
+    s->user = (cudaStream_t)cuda_stream;
+    if (cudaMallocHost((void**)&s->bits, sizeof(unsigned long long) * max_active) != cudaSuccess ||
+        cudaMallocHost((void**)&s->errs, sizeof(int) * max_active) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->bits) cudaFreeHost(s->bits);
+        delete s;
+        return MR_E_NOMEM;
+    }
+    for (int i = max_active - 1; i >= 0; --i) s->free_slots.push_back(i);
+    *out = s;
+    return MR_OK;
+}
+
+mr_status mr_server_submit(mr_server* s, const mr_config* cfg, const double* q0, double t_end, long long* id)
+{
+    if (!s || !cfg || !q0 || !id || !(t_end >= 0.0)) return MR_E_INVALID;
+    if (validate(cfg) != MR_OK) {
+        s->err = "submit: invalid configuration";
+        return MR_E_INVALID;
+    }
+    mr_request* q = new (std::nothrow) mr_request();
+    if (!q) return MR_E_NOMEM;
+    q->cfg = *cfg;
+    q->t_end = t_end;
+    q->bytes = projected_bytes(cfg);
+    if (q->bytes > s->budget) {
+        delete q;
+        s->err = "submit: the request alone exceeds the memory budget";
+        return MR_E_NOMEM;
+    }
+    const int m = cfg->equation == MR_EQ_EULER ? cfg->dim + 2 : 1;
+    const size_t n = (size_t)m << (cfg->dim * cfg->max_level);
+    q->q0.assign(q0, q0 + n);
+    q->id = s->next_id++;
+    s->queue.push_back(q);
+    s->all.push_back(q);
+    *id = q->id;
+    return MR_OK;
+}
+
+mr_status mr_server_advance(mr_server* s, int* n_active, int* n_queued)
+{
+    if (!s) return MR_E_INVALID;
+    reap(s);
+    MR_TRY(admit(s));
+    // every active request whose previous macro step has completed queues
+    // its next one (see progress_poll); nothing here waits
+    std::vector<mr_request*> still;
+    for (mr_request* q : s->active) {
+        progress_poll(q->h, q->t_end, &s->bits[q->slot], &s->errs[q->slot], q->ev, &q->pg);
+        if (q->pg.phase == PG_DONE) {
+            q->status = q->pg.status;
+            cudaEventRecord(q->fin, q->st);
+            q->state = 2;
+            s->finishing.push_back(q);
+        } else {
+            still.push_back(q);
+        }
+    }
+    s->active.swap(still);
+    reap(s);
+    if (n_active) *n_active = (int)(s->active.size() + s->finishing.size());
+    if (n_queued) *n_queued = (int)s->queue.size();
+    return MR_OK;
+}
+
+mr_status mr_server_poll(mr_server* s, long long* ids, int cap, int* n_done)
+{
+    if (!s || !n_done || (cap > 0 && !ids)) return MR_E_INVALID;
+    reap(s);
+    const int n = (int)s->completed.size() < cap ? (int)s->completed.size() : cap;
+    for (int i = 0; i < n; ++i) ids[i] = s->completed[i];
+    s->completed.erase(s->completed.begin(), s->completed.begin() + n);
+    *n_done = n;
+    return MR_OK;
+}
+
+mr_status mr_server_status(mr_server* s, long long id)
+{
+    if (!s) return MR_E_INVALID;
+    mr_request* q = find_request(s, id);
+    if (!q) return MR_E_INVALID;
+    return q->state == 3 ? q->status : MR_E_STATE;
+}
+
+mr_solver* mr_server_result(mr_server* s, long long id)
+{
+    if (!s) return nullptr;
+    mr_request* q = find_request(s, id);
+    return (q && q->state == 3) ? q->h : nullptr;
+}
+
+mr_status mr_server_release(mr_server* s, long long id)
+{
+    if (!s) return MR_E_INVALID;
+    for (size_t i = 0; i < s->all.size(); ++i) {
+        mr_request* q = s->all[i];
+        if (q->id != id) continue;
+        if (q->state != 3) return MR_E_STATE;
+        s->all.erase(s->all.begin() + i);
+        request_free(s, q);
+        return MR_OK;
+    }
+    return MR_E_INVALID;
+}
+
+size_t mr_server_memory(const mr_server* s) { return s ? s->used : 0; }
+
+const char* mr_server_last_error(const mr_server* s) { return s ? s->err.c_str() : kNullErr; }
+
+void mr_server_destroy(mr_server* s)
+{
+    if (!s) return;
+    for (mr_request* q : s->finishing) cudaEventSynchronize(q->fin);
+    for (mr_request* q : s->all) request_free(s, q);
+    if (s->bits) cudaFreeHost(s->bits);
+    if (s->errs) cudaFreeHost(s->errs);
+    delete s;
 }
 
 } // extern "C"

@@ -67,6 +67,7 @@ struct Grid {
     double eps;
     int eps_mode;
     int prec;                       // 0 FP64, 1 mixed: face fluxes in FP32
+    int flux;                       // Euler: 0 HLL, 1 AUSM+
 };
 
 // Programmatic dependent launch (sm_90 and later).  Every kernel starts by
@@ -362,6 +363,54 @@ __device__ __forceinline__ void recon_vars(const Grid& g, const double* W, R* P)
     }
 }
 
+// AUSM+ (Liou 1996), the paper's Euler flux (Sec. 5), across a face normal
+// to direction k, from the reconstructed primitives (rho, u_1..u_d, p) and
+// conservative states of both sides.  With total enthalpy H = (E + p)/rho
+// and critical speed a*^2 = 2 (g-1)/(g+1) H, the interface speed is
+// a = min(a*_L^2 / max(a*_L, u_L), a*_R^2 / max(a*_R, -u_R)); the Mach
+// numbers M = u/a are split as M+-(M) = +-(M +- 1)^2/4 +- (M^2 - 1)^2/8 and
+// pressure as P+-(M) = (M +- 1)^2 (2 -+ M)/4 +- 3/16 M (M^2 - 1)^2 when
+// |M| < 1 (upwind values otherwise); the flux is
+// a (max(m, 0) Psi_L + min(m, 0) Psi_R) + p_half e_k, Psi = rho (1, u, H),
+// m = M+(M_L) + M-(M_R), p_half = P+(M_L) p_L + P-(M_R) p_R.
+template <class R>
+__device__ __forceinline__ R ausm_split_mach(R M, R sgn)
+{
+    if (fabs(M) >= R(1)) return R(0.5) * (M + sgn * fabs(M));
+    const R t = M * M - R(1);
+    return sgn * R(0.25) * (M + sgn) * (M + sgn) + sgn * R(0.125) * t * t;
+}
+
+template <class R>
+__device__ __forceinline__ R ausm_split_pres(R M, R sgn)
+{
+    if (fabs(M) >= R(1)) return M * sgn > R(0) ? R(1) : R(0);
+    const R t = M * M - R(1);
+    return R(0.25) * (M + sgn) * (M + sgn) * (R(2) - sgn * M) + sgn * R(0.1875) * M * t * t;
+}
+
+template <int D, int M, class R>
+__device__ __forceinline__ void ausm_plus(R gam, int k, const R* PL, const R* PR, const R* UL, const R* UR, R* F)
+{
+    const R pL = PL[D + 1], pR = PR[D + 1];
+    const R HL = (UL[D + 1] + pL) / PL[0], HR = (UR[D + 1] + pR) / PR[0];
+    const R uL = PL[1 + k], uR = PR[1 + k];
+    const R cst = R(2) * (gam - R(1)) / (gam + R(1));
+    const R asL = sqrt(cst * HL), asR = sqrt(cst * HR);
+    const R atL = asL * asL / fmax(asL, uL);
+    const R atR = asR * asR / fmax(asR, -uR);
+    const R a = fmin(atL, atR);
+    const R ML = uL / a, MR = uR / a;
+    const R mh = ausm_split_mach(ML, R(1)) + ausm_split_mach(MR, R(-1));
+    const R ph = ausm_split_pres(ML, R(1)) * pL + ausm_split_pres(MR, R(-1)) * pR;
+    const R mp = fmax(mh, R(0)), mm = fmin(mh, R(0));
+    F[0] = a * (mp * PL[0] + mm * PR[0]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) F[1 + c] = a * (mp * UL[1 + c] + mm * UR[1 + c]);
+    F[D + 1] = a * (mp * (PL[0] * HL) + mm * (PR[0] * HR));
+    F[1 + k] += ph;
+}
+
 // Numerical flux along direction k across the face between stencil cells 1
 // and 2 of a 4-cell stencil, from their reconstruction variables P(i, v).
 template <int EQ, int D, int M, class R, class Acc>
@@ -403,6 +452,10 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
         UL[D + 1] = PL[D + 1] * igm + h * PL[0] * keL;
         UR[D + 1] = PR[D + 1] * igm + h * PR[0] * keR;
         const R unL = PL[1 + k], unR = PR[1 + k];
+        if (g.flux == 1) { // AUSM+
+            ausm_plus<D, M, R>(gam, k, PL, PR, UL, UR, F);
+            return;
+        }
 #pragma unroll
         for (int v = 0; v < M; ++v) {
             FL[v] = UL[v] * unL;

@@ -322,12 +322,12 @@ def serving_requests(n: int = 300, seed: int = 0, rate: float = 200.0) -> list:
                 cache[("b", L)] = burgers_1d(L=L, eps=eps, min_level=L - 7)
             p, q = cache[("b", L)]
             p = p.replace(eps=eps)
-            its = int(rng.integers(128, 513))
+            its = int(rng.integers(32, 129))
             t_end = its * 0.5 / (1 << L)            # speed max |u| = 1
         elif kind == 1:
             L = int(rng.integers(8, 11))
             p, q = rd_bumps_2d(L=L, eps=eps, seed=seed + i, rk_order=2, midpoint=True)
-            its = int(rng.integers(64, 257))
+            its = int(rng.integers(16, 65))
             dx = 1.0 / (1 << L)
             t_end = its * 0.5 * dx * dx / (4.0 * p.phys[0])  # diffusion limit
         else:
@@ -336,7 +336,7 @@ def serving_requests(n: int = 300, seed: int = 0, rate: float = 200.0) -> list:
                 cache[("e", L)] = euler_3d_blast(L=L, eps=eps, min_level=L - 4)
             p, q = cache[("e", L)]
             p = p.replace(eps=eps)
-            its = int(rng.integers(32, 97))
+            its = int(rng.integers(8, 25))
             t_end = its * 0.5 / (1 << L) / 4.0      # speed ~ 3.74
         p = p.replace(precision=PREC_MIXED, name=f"req{i}_{p.name}")
         out.append((t, p, q, float(t_end)))

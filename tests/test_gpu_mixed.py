@@ -135,6 +135,14 @@ def test_mixed_first_iterations_leafwise(case):
     _check_leafwise(p, q, dt, 3)
 
 
+def test_mixed_ausm_plus_leafwise():
+    p, q = I.euler_2d_quadrants(L=7, eps=1e-3, seed=0)
+    p = p.replace(flux=I.FLUX_AUSM_PLUS)
+    dt = 0.5 / 128 / 3.7
+    _check_leafwise(p, q, dt, 1)
+    _check_leafwise(p, q, dt, 3)
+
+
 def test_mixed_full_size_first_iterations_leafwise():
     """the 2D Euler L=10 workload: four fine iterations (lmin = 3, 10, 9, 10)"""
     p, q = I.euler_2d_quadrants(L=10, eps=1e-3, seed=0)

@@ -188,3 +188,23 @@ def test_euler_2d_full_size_macro_step():
     ref.iterate(dt, 124)
     assert_parity(gpu, ref, "L=10 after one macro step")
     assert gpu.stats()["macros"] == 1
+
+
+@pytest.mark.parametrize("mode,rk", [(I.TIME_LT, 3), (I.TIME_LT, 2), (I.TIME_GTS, 2)])
+def test_euler_2d_ausm_plus(mode, rk):
+    """the paper's Euler flux (AUSM+, Sec. 5) on the quadrant problem"""
+    p, q = I.euler_2d_quadrants(L=8, eps=1e-3, seed=0, rk_order=rk, time_mode=mode)
+    gpu, ref = _run_both(p.replace(flux=I.FLUX_AUSM_PLUS), q, t=0.05)
+    assert_parity(gpu, ref)
+
+
+def test_euler_1d_sod_ausm_plus():
+    p, q = I.euler_1d_sod(L=9, eps=1e-3)
+    gpu, ref = _run_both(p.replace(flux=I.FLUX_AUSM_PLUS), q, t=0.12)
+    assert_parity(gpu, ref)
+
+
+def test_euler_3d_ausm_plus():
+    p, q = I.euler_3d_blast(L=5, eps=1e-2, min_level=2, precision=I.PREC_FP64)
+    gpu, ref = _run_both(p.replace(flux=I.FLUX_AUSM_PLUS), q, t=0.01)
+    assert_parity(gpu, ref)
