@@ -62,6 +62,21 @@ def _args():
     return ap.parse_args()
 
 
+def replica_aggregate(dist, ws: int, total_s: float, e2e_s: float, updates: int, device: str = "cuda"):
+    """Whole-job figures of N independent replicas: the slowest rank's
+    device time and end-to-end time (all-reduce MAX over ranks) and the units
+    of all ranks over that time.  Every rank solves the same workload, so the
+    job's units are ws x the local count.  Returns (tmax, e2e_max, value,
+    e2e_value)."""
+    import torch
+    tmax = total_s
+    if dist is not None and ws > 1:
+        t = torch.tensor([total_s, e2e_s], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax, e2e_s = float(t[0]), float(t[1])
+    return tmax, e2e_s, ws * updates / tmax, ws * updates / e2e_s
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -369,13 +384,7 @@ def run_ours(args):
         solver._read(pkg.MR_READ_UNIFORM, np.float64, out=uni_pin)
         e2e_s += time.perf_counter() - t0
 
-    tmax = total_s
-    if dist is not None:
-        t = torch.tensor([total_s, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax, e2e_s = float(t[0]), float(t[1])
-    value = ws * updates / tmax
-    e2e_value = ws * updates / e2e_s
+    tmax, e2e_s, value, e2e_value = replica_aggregate(dist, ws, total_s, e2e_s, updates)
 
     if rank != 0:
         if dist is not None:

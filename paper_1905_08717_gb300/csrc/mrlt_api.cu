@@ -442,6 +442,7 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     g.eps_mode = cfg->eps_mode;
     g.prec = cfg->precision;
     g.flux = cfg->flux;
+    g.igm = cfg->equation == MR_EQ_EULER ? 1.0 / (cfg->phys[0] - 1.0) : 0.0;
     long long off = 0, toff = 0;
     for (int l = g.lb; l <= g.L; ++l) {
         g.toff[l] = toff;

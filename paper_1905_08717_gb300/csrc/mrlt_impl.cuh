@@ -68,6 +68,7 @@ struct Grid {
     int eps_mode;
     int prec;                       // 0 FP64, 1 mixed: face fluxes in FP32
     int flux;                       // Euler: 0 HLL, 1 AUSM+
+    double igm;                     // Euler: 1 / (gamma - 1)
 };
 
 // Programmatic dependent launch (sm_90 and later).  Every kernel starts by
@@ -448,7 +449,7 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
             keL += PL[1 + c] * PL[1 + c];
             keR += PR[1 + c] * PR[1 + c];
         }
-        const R igm = R(1) / (gam - R(1));
+        const R igm = R(g.igm);
         UL[D + 1] = PL[D + 1] * igm + h * PL[0] * keL;
         UR[D + 1] = PR[D + 1] * igm + h * PR[0] * keR;
         const R unL = PL[1 + k], unR = PR[1 + k];
@@ -465,8 +466,10 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
         FR[1 + k] += PR[D + 1];
         FL[D + 1] += PL[D + 1] * unL;
         FR[D + 1] += PR[D + 1] * unR;
-        const R cL = sqrt(gam * PL[D + 1] / PL[0]);
-        const R cR = sqrt(gam * PR[D + 1] / PR[0]);
+        // sound speeds sqrt(gamma p / rho) = gamma p rsqrt(gamma p rho)
+        const R gpL = gam * PL[D + 1], gpR = gam * PR[D + 1];
+        const R cL = gpL * rsqrt(gpL * PL[0]);
+        const R cR = gpR * rsqrt(gpR * PR[0]);
         const R sL = fmin(unL - cL, unR - cR);
         const R sR = fmax(unL + cL, unR + cR);
         if (sL >= R(0)) {
