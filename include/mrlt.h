@@ -90,7 +90,9 @@ typedef struct mr_config {
  * projection (Eq. 3) and, unless adapt_mode == MR_ADAPT_NEVER, the tree is
  * adapted once (Algs. 1-2).  q0 is read only during the call.
  * Returns MR_E_INVALID for a bad configuration, MR_E_NOMEM when device memory
- * is insufficient.  *out receives the handle (NULL on failure). */
+ * is insufficient: the exact footprint of the configuration is compared with
+ * the free device memory before anything is allocated or q0 is read.  *out
+ * receives the handle (NULL on failure). */
 mr_status mr_create(const mr_config* cfg, const double* q0_finest, void* cuda_stream,
                     mr_solver** out);
 

@@ -509,6 +509,18 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
     if (!out) return MR_E_INVALID;
     *out = nullptr;
     if (validate(cfg) != MR_OK || !q0) return MR_E_INVALID;
+    {
+        // the exact footprint, projected before anything is allocated or read
+        mr_solver probe;
+        probe.dry = true;
+        layout_alloc(&probe, cfg);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && probe.bytes > free_b) {
+            fprintf(stderr, "mr_create: needs %zu bytes of device memory, %zu free\n", probe.bytes, free_b);
+            return MR_E_NOMEM;
+        }
+        cudaGetLastError();
+    }
     mr_solver* h = new (std::nothrow) mr_solver();
     if (!h) return MR_E_NOMEM;
     h->cfg = *cfg;

@@ -29,6 +29,9 @@ constexpr int NTHREADS = 128;
 constexpr int kTile1X = 64;
 constexpr int kTile2X = 16, kTile2Y = 8;
 constexpr int kTile3X = 8, kTile3Y = 4, kTile3Z = 4;
+// threads per tile CTA: two per cell (measured: 3D blast L=8 -10 to -13%, 2D
+// Euler L=10 -1.5% against one per cell; four per cell was slower)
+constexpr int kTileThreads1 = 128, kTileThreads2 = 256, kTileThreads3 = 256;
 
 enum Field { F_Q0 = 0, F_Q1, F_Q2, F_QE, F_XH, F_NH, F_N1, F_N3, NFIELD };
 enum Kind { K_WALL = 0, K_LEAF = 1, K_FINER = 2, K_COARSER = 3 };

@@ -49,12 +49,14 @@ __device__ __forceinline__ void reg_add(const Grid& g, int u, long long id, int 
     for (int v = 0; v < M; ++v) R[(fi * M + v) * N] += bw * F[v];
 }
 
-// Tile shapes of the tiled stage kernel: a CTA owns TX x TY x TZ cells of one
-// level (the same shapes index the per-level active-tile lists).
+// Tile shapes of the tiled stage kernel: a CTA of THREADS threads owns
+// TX x TY x TZ cells of one level (the same shapes index the per-level
+// active-tile lists); THREADS may exceed the cell count, so that the list,
+// exposure and face phases spread over more threads.
 template <int D> struct Tile;
-template <> struct Tile<1> { static constexpr int TX = kTile1X, TY = 1, TZ = 1; };
-template <> struct Tile<2> { static constexpr int TX = kTile2X, TY = kTile2Y, TZ = 1; };
-template <> struct Tile<3> { static constexpr int TX = kTile3X, TY = kTile3Y, TZ = kTile3Z; };
+template <> struct Tile<1> { static constexpr int TX = kTile1X, TY = 1, TZ = 1, THREADS = kTileThreads1; };
+template <> struct Tile<2> { static constexpr int TX = kTile2X, TY = kTile2Y, TZ = 1, THREADS = kTileThreads2; };
+template <> struct Tile<3> { static constexpr int TX = kTile3X, TY = kTile3Y, TZ = kTile3Z, THREADS = kTileThreads3; };
 
 // Block (tile + 2-cell ring) and face counts of one tile; the three large
 // shared arrays (conservative values, reconstruction variables, face fluxes)
@@ -62,7 +64,9 @@ template <> struct Tile<3> { static constexpr int TX = kTile3X, TY = kTile3Y, TZ
 template <int EQ, int D, class R>
 struct TileShape {
     static constexpr int M = EQ == 2 ? D + 2 : 1;
-    static constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, NT = TX * TY * TZ, H = 2;
+    static constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ, H = 2;
+    static constexpr int NC = TX * TY * TZ, NT = Tile<D>::THREADS; // cells, threads
+    static_assert(NT % 32 == 0 && NT >= NC, "whole warps, at least one thread per cell");
     static constexpr int BX = TX + 2 * H, BY = D > 1 ? TY + 2 * H : 1, BZ = D > 2 ? TZ + 2 * H : 1;
     static constexpr int NB = BX * BY * BZ;
     static constexpr int NFX = (TX + 1) * TY * TZ;
@@ -124,7 +128,7 @@ __device__ __forceinline__ void block_append2(bool ta, bool tb, int item, short*
 //  4. applies the compact RK update and the register epilogue to its leaves.
 // Work lists keep every warp on one kind of work.
 template <int EQ, int D, class R>
-__global__ void __launch_bounds__(Tile<D>::TX * Tile<D>::TY * Tile<D>::TZ)
+__global__ void __launch_bounds__(Tile<D>::THREADS)
 k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
 {
     pdl_enter();
@@ -246,7 +250,7 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
     }
     __syncthreads();
     const int nleaf = __syncthreads_count(
-        tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0));
+        tid < S::NC && tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0));
     if (nleaf == 0) continue; // uniform across the CTA
     if (tid == 0) {
         if (s == 1) atomicAdd(g.updates, (unsigned long long)nleaf);
@@ -387,8 +391,8 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
     }
     __syncthreads();
 
-    // 4. compact RK update of the tile's leaves
-    {
+    // 4. compact RK update of the tile's leaves (thread tid < NC owns cell tid)
+    if (tid < S::NC) {
         const int i = tid % TX, j = D > 1 ? (tid / TX) % TY : 0, kz = D > 2 ? tid / (TX * TY) : 0;
         const int bx = H + i, by = D > 1 ? H + j : 0, bz = D > 2 ? H + kz : 0;
         const int b = bz * SZ + by * SY + bx;

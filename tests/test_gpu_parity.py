@@ -208,3 +208,33 @@ def test_euler_3d_ausm_plus():
     p, q = I.euler_3d_blast(L=5, eps=1e-2, min_level=2, precision=I.PREC_FP64)
     gpu, ref = _run_both(p.replace(flux=I.FLUX_AUSM_PLUS), q, t=0.01)
     assert_parity(gpu, ref)
+
+
+def test_largest_1d_grid():
+    """the finest 1D grid the layout allows (L = 16, 65536 cells), LT/NERK3"""
+    p, q = I.burgers_1d(L=16, eps=1e-3, min_level=10)
+    gpu, ref = _run_both(p, q)
+    dt = 0.5 / (1 << 16)
+    gpu.iterate(dt, 8)
+    ref.iterate(dt, 8)
+    assert_parity(gpu, ref)
+
+
+def test_oversize_problem_reports_nomem():
+    """a 3D Euler problem at L = 10 needs about 1 TB: creation fails with
+    MR_E_NOMEM before anything is allocated or read (a one-element buffer
+    stands in for the finest data), and the device stays usable"""
+    import ctypes
+    import paper_1905_08717_gb300 as pkg
+    p = I.Problem(dim=3, equation=I.EQ_EULER, max_level=10, min_level=9, eps=1e-3,
+                  bc=(I.BC_NEUMANN,) * 3, phys=(1.4,) + (0.0,) * 7)
+    lib = pkg.library()
+    cfg = pkg.make_config(p)
+    tiny = np.zeros(1)
+    h = ctypes.c_void_p()
+    r = lib.mr_create(ctypes.byref(cfg), tiny.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None,
+                      ctypes.byref(h))
+    assert r == 2 and not h.value  # MR_E_NOMEM, no handle
+    p2, q2 = I.burgers_1d(L=8, eps=1e-3)
+    gpu, ref = _run_both(p2, q2, t=0.05)  # the device still works
+    assert_parity(gpu, ref)
