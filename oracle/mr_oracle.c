@@ -76,10 +76,12 @@ static void coords(const Orc* o, int l, long id, int c[3])
     if (o->d < 2) c[1] = 0;
 }
 
-/* ghost-cell rule applied identically on every level (READING: the paper
- * states boundary conditions only for the PDE, Sec. 5): periodic wrap, or
- * homogeneous Neumann as an even mirror about the wall. */
-static int mirror(const Orc* o, int l, int k, int p)
+/* ghost rule (the paper states boundary conditions only for the PDE; the
+ * same rule is used on every level): periodic wrap; homogeneous Neumann as an
+ * even mirror about the wall; zero Dirichlet as an odd mirror, the ghost
+ * taking the negated value, so that *sgn changes sign at every reflection on
+ * a Dirichlet wall. */
+static int mirror_s(const Orc* o, int l, int k, int p, double* sgn)
 {
     int n = o->n[l];
     if (o->cfg.bc[k] == 0) {
@@ -89,7 +91,8 @@ static int mirror(const Orc* o, int l, int k, int p)
     }
     while (p < 0 || p >= n) {
         if (p < 0) p = -1 - p;
-        if (p >= n) p = 2 * n - 1 - p;
+        else p = 2 * n - 1 - p;
+        if (o->cfg.bc[k] == 2) *sgn = -*sgn;
     }
     return p;
 }
@@ -202,7 +205,8 @@ static void predict_cell(Orc* o, int l, const int q[3], const Ctx* x, double* ou
                 int idx = (dz + 1) * 9 + (dy + 1) * 3 + (dxx + 1);
                 if ((d < 3 && dz != 0) || (d < 2 && dy != 0)) continue;
                 int p[3] = {0, 0, 0}, off[3] = {dxx, dy, dz};
-                for (k = 0; k < d; k++) p[k] = mirror(o, l - 1, k, P[k] + off[k]);
+                double sg = 1.0;
+                for (k = 0; k < d; k++) p[k] = mirror_s(o, l - 1, k, P[k] + off[k], &sg);
                 long id = lin(o, l - 1, p);
                 if (o->st[l - 1][id] == 0) {
                     fail(o, "predict: source (%d,%d,%d) at level %d absent", p[0], p[1], p[2], l - 1);
@@ -210,6 +214,8 @@ static void predict_cell(Orc* o, int l, const int q[3], const Ctx* x, double* ou
                     continue;
                 }
                 expose(o, l - 1, id, x, B[idx]);
+                if (sg < 0.0)
+                    for (v = 0; v < m; v++) B[idx][v] = -B[idx][v];
             }
     /* collapse along x */
     double R[9][MMAX];
@@ -252,11 +258,14 @@ static void predict_cell(Orc* o, int l, const int q[3], const Ctx* x, double* ou
  * from the parent level (Sec. 2, virtual leaves). */
 static void value_at(Orc* o, int l, const int p[3], const Ctx* x, double* out)
 {
-    int q[3] = {0, 0, 0}, k;
-    for (k = 0; k < o->d; k++) q[k] = mirror(o, l, k, p[k]);
+    int q[3] = {0, 0, 0}, k, v;
+    double sg = 1.0;
+    for (k = 0; k < o->d; k++) q[k] = mirror_s(o, l, k, p[k], &sg);
     long id = lin(o, l, q);
     if (o->st[l][id]) expose(o, l, id, x, out);
     else predict_cell(o, l, q, x, out);
+    if (sg < 0.0)
+        for (v = 0; v < o->m; v++) out[v] = -out[v];
 }
 
 /* ------------------------------------------------------------ physics */
@@ -1148,6 +1157,12 @@ int or_create(const or_config* cfg, const double* q0, void** out)
         cfg->dim * cfg->max_level > 30 || cfg->flux < 0 || cfg->flux > 1 ||
         (cfg->flux == 1 && cfg->equation != 2))
         return OR_E_INVALID;
+    {
+        int k;
+        for (k = 0; k < cfg->dim; k++)
+            if (cfg->bc[k] < 0 || cfg->bc[k] > 2 || (cfg->bc[k] == 2 && cfg->equation == 2))
+                return OR_E_INVALID; /* zero Dirichlet: scalar equations only */
+    }
     Orc* o = (Orc*)calloc(1, sizeof(Orc));
     if (!o) return OR_E_NOMEM;
     o->cfg = *cfg;

@@ -35,7 +35,8 @@ typedef struct or_config {
     int    reflux;      /* 1: conservative flux registers at coarse-fine faces */
     double cfl;         /* Courant number sigma                               */
     double lo[3], hi[3];/* box                                                */
-    int    bc[3];       /* 0 periodic, 1 homogeneous Neumann (mirror)         */
+    int    bc[3];       /* 0 periodic, 1 homogeneous Neumann (even mirror),
+                           2 zero Dirichlet (odd mirror; scalar equations)    */
     double phys[8];     /* advection: a_x,a_y,a_z | Euler: gamma | RD: D,k,a  */
     int    flux;        /* 0: the equation's default flux (Euler: HLL);
                            1: AUSM+ (Euler only), the paper's flux (Sec. 5)   */

@@ -141,3 +141,47 @@ def exact_riemann(left, right, gamma, xi):
                     v = (rr * (c / cr) ** (2.0 / (g - 1.0)), uu, pr * (c / cr) ** (2.0 * g / (g - 1.0)))
         out_r[i], out_u[i], out_p[i] = v
     return out_r, out_u, out_p
+
+
+def _pad(u, axis, bc):
+    """two ghost cells per side along axis: periodic wrap, Neumann even
+    mirror, zero-Dirichlet odd mirror"""
+    pw = [(0, 0)] * u.ndim
+    pw[axis] = (2, 2)
+    if bc == 0:
+        return np.pad(u, pw, mode="wrap")
+    g = np.pad(u, pw, mode="symmetric")
+    if bc == 2:
+        idx = [slice(None)] * u.ndim
+        idx[axis] = slice(0, 2)
+        g[tuple(idx)] *= -1.0
+        idx[axis] = slice(-2, None)
+        g[tuple(idx)] *= -1.0
+    return g
+
+
+def burgers_rhs_nd(u, h, bc):
+    """-div F for u_t + sum_k (u^2/2)_{x_k} = 0 on a uniform grid of any
+    dimension (array axes = directions), MUSCL-minmod + Godunov per direction,
+    ghost cells per bc[axis]."""
+    out = np.zeros_like(u)
+    for ax in range(u.ndim):
+        g = _pad(u, ax, bc[ax])
+        n = u.shape[ax]
+
+        def sl(a, b):
+            idx = [slice(None)] * u.ndim
+            idx[ax] = slice(a, b)
+            return g[tuple(idx)]
+        # faces f = 0..n between padded cells f+1 and f+2 (stencil f .. f+3)
+        um, u0, u1, u2 = sl(0, n + 1), sl(1, n + 2), sl(2, n + 3), sl(3, n + 4)
+        uL = u0 + 0.5 * _minmod(u0 - um, u1 - u0)
+        uR = u1 - 0.5 * _minmod(u1 - u0, u2 - u1)
+        fL, fR = 0.5 * uL ** 2, 0.5 * uR ** 2
+        F = np.where(uL <= uR, np.where(uL > 0, fL, np.where(uR < 0, fR, 0.0)), np.maximum(fL, fR))
+        idx_hi = [slice(None)] * u.ndim
+        idx_lo = [slice(None)] * u.ndim
+        idx_hi[ax] = slice(1, n + 1)
+        idx_lo[ax] = slice(0, n)
+        out -= (F[tuple(idx_hi)] - F[tuple(idx_lo)]) / h
+    return out
