@@ -47,7 +47,10 @@ typedef enum {
 } mr_status;
 
 enum { MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_EULER = 2, MR_EQ_REACTION_DIFFUSION = 3 };
-enum { MR_BC_PERIODIC = 0, MR_BC_NEUMANN = 1 };
+/* Walls: periodic wrap; homogeneous Neumann (even mirror ghost cells); zero
+ * Dirichlet (odd mirror: a ghost takes the negated value; scalar equations
+ * only), the same rule on every level. */
+enum { MR_BC_PERIODIC = 0, MR_BC_NEUMANN = 1, MR_BC_DIRICHLET0 = 2 };
 enum { MR_TIME_GTS = 0, MR_TIME_LT_NERK = 1 };
 enum { MR_ADAPT_NEVER = 0, MR_ADAPT_MACRO = 1, MR_ADAPT_EVERY = 2 };
 /* Arithmetic of the stage kernels.  MR_PREC_MIXED evaluates the MUSCL

@@ -90,7 +90,9 @@ mr_status validate(const mr_config* c)
     if (!(c->cfl > 0.0) || !(c->eps >= 0.0)) return MR_E_INVALID;
     for (int k = 0; k < c->dim; ++k) {
         if (!(c->hi[k] > c->lo[k])) return MR_E_INVALID;
-        if (c->bc[k] != MR_BC_PERIODIC && c->bc[k] != MR_BC_NEUMANN) return MR_E_INVALID;
+        if (c->bc[k] != MR_BC_PERIODIC && c->bc[k] != MR_BC_NEUMANN && c->bc[k] != MR_BC_DIRICHLET0)
+            return MR_E_INVALID;
+        if (c->bc[k] == MR_BC_DIRICHLET0 && c->equation == MR_EQ_EULER) return MR_E_INVALID;
     }
     if (c->equation == MR_EQ_EULER && !(c->phys[0] > 1.0)) return MR_E_INVALID;
     return MR_OK;

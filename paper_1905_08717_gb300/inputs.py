@@ -25,6 +25,7 @@ EQ_REACTION_DIFFUSION = 3
 
 BC_PERIODIC = 0
 BC_NEUMANN = 1
+BC_DIRICHLET0 = 2  # zero Dirichlet: odd-mirror ghost cells (scalar equations)
 
 TIME_GTS = 0
 TIME_LT = 1
@@ -130,9 +131,10 @@ def burgers_1d(L: int = 10, eps: float = 1e-3, min_level: int = 2,
 
 def burgers_2d(L: int = 7, eps: float = 1e-2, min_level: int = 2,
                rk_order: int = 3, time_mode: int = TIME_LT,
-               t_end: float = 0.2) -> tuple[Problem, np.ndarray]:
-    """2D inviscid Burgers on [0,1]^2 with u0 = sin(2 pi x) sin(2 pi y), periodic
-    (the paper's Sec. 5.1 case uses Dirichlet walls; periodic keeps mass exact)."""
+               t_end: float = 0.2, bc: int = BC_PERIODIC) -> tuple[Problem, np.ndarray]:
+    """2D inviscid Burgers on [0,1]^2 with u0 = sin(2 pi x) sin(2 pi y), exact
+    cell averages.  The paper's Sec. 5.1 case has u = 0 on the walls
+    (bc=BC_DIRICHLET0, see burgers_2d_paper); periodic keeps mass exact."""
     n = 1 << L
     h = 1.0 / n
     a = np.arange(n) * h
@@ -140,9 +142,20 @@ def burgers_2d(L: int = 7, eps: float = 1e-2, min_level: int = 2,
     u = s[:, None] * s[None, :]
     p = Problem(dim=2, equation=EQ_BURGERS, max_level=L, min_level=min_level,
                 eps=eps, eps_mode=0, rk_order=rk_order, time_mode=time_mode,
-                cfl=0.5, bc=(BC_PERIODIC,) * 3, t_end=t_end,
+                cfl=0.5, bc=(bc,) * 3, t_end=t_end,
                 name=f"burgers2d_L{L}")
     return p, u[None, :, :].copy()
+
+
+def burgers_2d_paper(L: int = 10, eps: float = 1e-3, min_level: int = 3, rk_order: int = 2,
+                     time_mode: int = TIME_LT, t_end: float = 0.9) -> tuple[Problem, np.ndarray]:
+    """The paper's 2D Burgers case (Sec. 5.1): sin(2 pi x) sin(2 pi y) on
+    [0,1]^2, u = 0 on the walls, to t = 0.9 (its figure's final time), CFL 0.5.
+    The paper's flux there is AUSM+; this build uses MUSCL-minmod + Godunov for
+    Burgers."""
+    p, q = burgers_2d(L=L, eps=eps, min_level=min_level, rk_order=rk_order,
+                      time_mode=time_mode, t_end=t_end, bc=BC_DIRICHLET0)
+    return p.replace(name=f"burgers2d_paper_L{L}"), q
 
 
 # Lax-Liu configuration 6 (Table 8): quadrants 1..4 = [.5,1]x[.5,1], [0,.5]x[.5,1],

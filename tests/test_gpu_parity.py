@@ -238,3 +238,23 @@ def test_oversize_problem_reports_nomem():
     p2, q2 = I.burgers_1d(L=8, eps=1e-3)
     gpu, ref = _run_both(p2, q2, t=0.05)  # the device still works
     assert_parity(gpu, ref)
+
+
+@pytest.mark.parametrize("mode,rk", [(I.TIME_LT, 2), (I.TIME_LT, 3), (I.TIME_GTS, 2)])
+def test_burgers_2d_paper_case_dirichlet(mode, rk):
+    """the paper's 2D Burgers case (Sec. 5.1, u = 0 on the walls), reduced size"""
+    p, q = I.burgers_2d_paper(L=7, eps=1e-3, min_level=3, rk_order=rk, time_mode=mode)
+    gpu, ref = _run_both(p, q, t=0.25)
+    assert_parity(gpu, ref)
+
+
+def test_burgers_1d_dirichlet():
+    p, q = I.burgers_1d(L=10, eps=1e-3)
+    gpu, ref = _run_both(p.replace(bc=(I.BC_DIRICHLET0,) * 3), q, t=0.3)
+    assert_parity(gpu, ref)
+
+
+def test_rd_2d_dirichlet():
+    p, q = I.rd_bumps_2d(L=7, eps=1e-3, seed=4)
+    gpu, ref = _run_both(p.replace(bc=(I.BC_DIRICHLET0,) * 3), q, t=0.03)
+    assert_parity(gpu, ref)
