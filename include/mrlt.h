@@ -111,6 +111,19 @@ mr_status mr_reset(mr_solver* h, const double* q0_finest);
  * Only allowed at a macro-step boundary. */
 mr_status mr_set_tree(mr_solver* h, const unsigned char* leaf_level_finest);
 
+/* Checkpoint / resume.  At a macro-step boundary every leaf is at the same
+ * time t, the flux registers are applied and empty, and internal nodes are
+ * projections of the leaves, so the leaves' keys and values (MR_READ_LEAF_KEYS,
+ * MR_READ_LEAF_VALUES), t and the fine-iteration count (MR_READ_STATS) are the
+ * whole state.  This creates a solver from such a state: keys int32
+ * [n_leaves][4] and values double [n_leaves][m] (host, read during the call),
+ * cfg as at the original creation.  The run then continues exactly as the
+ * original one would (bit for bit on the same GPU).  MR_E_INVALID unless the
+ * keys are a graded partition of the box into leaves; MR_E_STATE if iters is
+ * not a multiple of the macro step 2^{L-min}.  The paper has no counterpart. */
+mr_status mr_create_from_state(const mr_config* cfg, long long n_leaves, const int* keys, const double* values,
+                               double t, long long iters, void* cuda_stream, mr_solver** out);
+
 /* Full adaptation (Algs. 1-2) at the current synchronised time. */
 mr_status mr_adapt(mr_solver* h);
 

@@ -70,6 +70,9 @@ def library() -> ctypes.CDLL:
         lib.mr_leaf_mass_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double), vp, vp, ll, ctypes.c_int,
                                              vp, vp, ctypes.c_char_p, ctypes.c_size_t]
+        lib.mr_create_from_state.argtypes = [ctypes.POINTER(mr_config), ll, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_double, ll, vp,
+                                             ctypes.POINTER(vp)]
         lib.mr_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(mr_config),
                                         ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), vp,
                                         ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)]
@@ -94,7 +97,7 @@ def library() -> ctypes.CDLL:
         lib.mr_server_last_error.restype = ctypes.c_char_p
         lib.mr_server_destroy.argtypes = [vp]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
-                     "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create",
+                     "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create", "mr_create_from_state",
                      "mr_batch_step", "mr_server_create", "mr_server_submit", "mr_server_advance",
                      "mr_server_poll", "mr_server_status", "mr_server_release"):
             getattr(lib, name).restype = ctypes.c_int
@@ -158,6 +161,31 @@ class Solver:
                           ctypes.byref(self._h))
         if r != 0:
             raise MRError(r, "mr_create failed")
+
+    @classmethod
+    def from_state(cls, problem, keys: np.ndarray, values: np.ndarray, t: float, iters: int, stream=None):
+        """Resume from a state saved at a macro-step boundary (see state())."""
+        lib = library()
+        self = cls.__new__(cls)
+        self.p = problem
+        self.m = problem.nvars()
+        k = np.ascontiguousarray(keys, dtype=np.int32).reshape(-1, 4)
+        v = np.ascontiguousarray(values, dtype=np.float64).reshape(-1, self.m)
+        self._cfg = make_config(problem)
+        self._h = ctypes.c_void_p()
+        r = lib.mr_create_from_state(ctypes.byref(self._cfg), len(k), k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     _dptr(v), float(t), int(iters), ctypes.c_void_p(_stream_handle(stream)),
+                                     ctypes.byref(self._h))
+        if r != 0:
+            raise MRError(r, "mr_create_from_state failed")
+        return self
+
+    def state(self):
+        """(keys, values, t, iters): everything needed to resume at a
+        macro-step boundary with from_state()"""
+        k, v = self.leaves()
+        st = self.stats()
+        return k, v, st["t"], st["iters"]
 
     @classmethod
     def _view(cls, problem, handle: int, owner):

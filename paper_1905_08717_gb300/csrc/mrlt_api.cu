@@ -630,6 +630,73 @@ mr_status mr_set_tree(mr_solver* h, const unsigned char* lev)
     return sync_check(h);
 }
 
+mr_status mr_create_from_state(const mr_config* cfg, long long n_leaves, const int* keys, const double* values,
+                               double t, long long iters, void* cuda_stream, mr_solver** out)
+{
+    if (!out) return MR_E_INVALID;
+    *out = nullptr;
+    if (validate(cfg) != MR_OK || n_leaves < 1 || !keys || !values || !(t >= 0.0) || iters < 0)
+        return MR_E_INVALID;
+    const int d = cfg->dim, L = cfg->max_level, lb = cfg->min_level;
+    const int m = cfg->equation == MR_EQ_EULER ? d + 2 : 1;
+    if (iters % (1LL << (L - lb)) != 0) return MR_E_STATE; // not a macro-step boundary
+    // finest-level leaf map: every finest cell covered by exactly one leaf
+    const long long nL = 1LL << L, NL = 1LL << (d * L);
+    std::vector<unsigned char> map((size_t)NL, 0xff);
+    for (long long i = 0; i < n_leaves; ++i) {
+        const int* K = keys + 4 * i;
+        const int l = K[0];
+        if (l < lb || l > L) return MR_E_INVALID;
+        const long long span = 1LL << (L - l);
+        long long lo3[3] = {0, 0, 0}, hi3[3] = {1, 1, 1};
+        for (int k = 0; k < d; ++k) {
+            if (K[1 + k] < 0 || K[1 + k] >= (1LL << l)) return MR_E_INVALID;
+            lo3[k] = K[1 + k] * span;
+            hi3[k] = lo3[k] + span;
+        }
+        for (long long z = lo3[2]; z < hi3[2]; ++z)
+            for (long long y = lo3[1]; y < hi3[1]; ++y)
+                for (long long x = lo3[0]; x < hi3[0]; ++x) {
+                    unsigned char& c = map[(size_t)(x + nL * (y + nL * z))];
+                    if (c != 0xff) return MR_E_INVALID; // overlapping leaves
+                    c = (unsigned char)l;
+                }
+    }
+    for (unsigned char c : map)
+        if (c == 0xff) return MR_E_INVALID; // a hole in the partition
+    // a solver on zero data without adaptation, then the saved tree and values
+    mr_config c0 = *cfg;
+    c0.adapt_mode = MR_ADAPT_NEVER;
+    std::vector<double> zeros((size_t)m * NL, 0.0);
+    mr_solver* h = nullptr;
+    MR_TRY(mr_create(&c0, zeros.data(), cuda_stream, &h));
+    h->cfg = *cfg;
+    mr_status r = mr_set_tree(h, map.data());
+    Grid& g = h->K.g;
+    if (r == MR_OK && cudaMemcpyAsync(h->d_keys, keys, sizeof(int) * 4 * (size_t)n_leaves, cudaMemcpyHostToDevice,
+                                      h->stream) != cudaSuccess)
+        r = MR_E_CUDA;
+    if (r == MR_OK && cudaMemcpyAsync(h->d_T, values, sizeof(double) * (size_t)m * n_leaves,
+                                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        r = MR_E_CUDA;
+    if (r == MR_OK) {
+        h->K.set_leaves(h->d_keys, h->d_T, n_leaves);
+        for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
+        h->t = t;
+        h->iters = iters;
+        h->macros = iters >> (L - lb);
+        h->pos = 0;
+        r = sync_check(h);
+    }
+    (void)g;
+    if (r != MR_OK) {
+        mr_destroy(h);
+        return r;
+    }
+    *out = h;
+    return MR_OK;
+}
+
 mr_status mr_adapt(mr_solver* h)
 {
     if (!h) return MR_E_INVALID;

@@ -832,6 +832,39 @@ __global__ void k_set_dt(Grid g, double dt)
     if (threadIdx.x == 0) *g.dtp = dt;
 }
 
+// leaf values from (level, i, j, k) keys: q^n and the end value of each leaf
+// (restoring a state saved at a macro-step boundary); a key that is not a
+// leaf of the installed tree sets ERR_INDEX
+__global__ void k_set_leaves(Grid g, const int* keys, const double* vals, long long n)
+{
+    pdl_enter();
+    GRID_STRIDE(t, n)
+    {
+        const int* K = keys + 4 * t;
+        const int l = K[0];
+        if (l < g.lb || l > g.L || K[1] < 0 || K[1] >= g.n[l] || (g.d > 1 && (K[2] < 0 || K[2] >= g.n[l])) ||
+            (g.d > 2 && (K[3] < 0 || K[3] >= g.n[l]))) {
+            atomicOr(g.err, ERR_INDEX);
+            continue;
+        }
+        const long long id = cell_id(g, l, K[1], g.d > 1 ? K[2] : 0, g.d > 2 ? K[3] : 0);
+        if (status(g, l, id) != 1) {
+            atomicOr(g.err, ERR_INDEX);
+            continue;
+        }
+        const long long N = g.N[l];
+        double* q0 = fbase_w(g, F_Q0, l) + id;
+        double* qe = fbase_w(g, F_QE, l) + id;
+        for (int v = 0; v < g.m; ++v) q0[v * N] = qe[v * N] = vals[t * g.m + v];
+    }
+}
+
+void Launcher::set_leaves(const int* keys, const double* vals, long long count)
+{
+    pdl_launch(k_set_leaves, blocks_dense(count), NTHREADS, 0, st, g, keys, vals, count);
+    ++n;
+}
+
 void Launcher::scale_init()
 {
     pdl_launch(k_scale_init, 1, 32, 0, st, g);
