@@ -98,6 +98,49 @@ mr_status validate(const mr_config* c)
     return MR_OK;
 }
 
+// Solver memory comes from a library-private, stream-ordered memory pool per
+// device that keeps freed memory cached: creating and destroying solvers
+// (batches, a server admitting and releasing requests) then never calls
+// cudaMalloc or cudaFree, whose device-wide synchronisation would stall the
+// other solvers' work in flight.  The cached memory stays reserved until the
+// process exits.
+constexpr int kMaxPoolDevices = 64;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+
+cudaMemPool_t device_pool()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull; // never release cached memory at synchronisation
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+// bytes the pool holds cached (reserved, not in use) on the current device
+size_t pool_cached_bytes()
+{
+    cudaMemPool_t pool = device_pool();
+    unsigned long long reserved = 0, used = 0;
+    if (!pool || cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 template <class T>
 mr_status dev_alloc(mr_solver* h, T** p, size_t count)
 {
@@ -105,9 +148,11 @@ mr_status dev_alloc(mr_solver* h, T** p, size_t count)
     if (count == 0) return MR_OK;
     h->bytes += (count * sizeof(T) + 255) / 256 * 256;
     if (h->dry) return MR_OK;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    cudaMemPool_t pool = device_pool();
+    cudaError_t e = pool ? cudaMallocFromPoolAsync((void**)p, count * sizeof(T), pool, h->stream)
+                         : cudaErrorMemoryAllocation;
     if (e != cudaSuccess) {
-        h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        h->err = std::string("device allocation: ") + cudaGetErrorString(e);
         *p = nullptr;
         cudaGetLastError();
         return MR_E_NOMEM;
@@ -175,9 +220,9 @@ mr_status sync_check(mr_solver* h)
         return MR_E_CUDA;
     }
     MR_CK(cudaGetLastError());
-    MR_CK(cudaStreamSynchronize(h->stream));
     int e = 0;
-    MR_CK(cudaMemcpy(&e, h->K.g.err, sizeof(int), cudaMemcpyDeviceToHost));
+    MR_CK(cudaMemcpyAsync(&e, h->K.g.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaStreamSynchronize(h->stream));
     if (e) {
         char buf[128];
         snprintf(buf, sizeof buf, "device reported error bits 0x%x", e);
@@ -490,7 +535,8 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     A(dev_alloc(h, &g.wmax, 1));
     A(dev_alloc(h, &g.updates, 1));
     A(dev_alloc(h, &g.work, (LMAX + 1) * 4));
-    if (r == MR_OK && !h->dry && cudaMemset(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long)) != cudaSuccess)
+    if (r == MR_OK && !h->dry &&
+        cudaMemsetAsync(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long), h->stream) != cudaSuccess)
         r = MR_E_CUDA; // cumulative counters: never cleared by mr_reset
     long long nblk = 0;
     for (int l = g.lb; l <= g.L; ++l) nblk += (g.N[l] + NTHREADS - 1) / NTHREADS;
@@ -517,7 +563,7 @@ mr_status mr_create(const mr_config* cfg, const double* q0, void* cuda_stream, m
         probe.dry = true;
         layout_alloc(&probe, cfg);
         size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && probe.bytes > free_b) {
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && probe.bytes > free_b + pool_cached_bytes()) {
             fprintf(stderr, "mr_create: needs %zu bytes of device memory, %zu free\n", probe.bytes, free_b);
             return MR_E_NOMEM;
         }
@@ -841,7 +887,8 @@ mr_status mr_profile(mr_solver* h, int enable)
         for (double& x : h->prof_level_ms) x = 0.0;
         h->prof_launches = 0;
         h->prof_all0 = h->K.n + h->stage_launches;
-        MR_CK(cudaMemcpy(h->work0, h->K.g.work, sizeof h->work0, cudaMemcpyDeviceToHost));
+        MR_CK(cudaMemcpyAsync(h->work0, h->K.g.work, sizeof h->work0, cudaMemcpyDeviceToHost, h->stream));
+        MR_CK(cudaStreamSynchronize(h->stream));
         h->prof = true;
     } else {
         drain_events(h);
@@ -856,7 +903,7 @@ void mr_destroy(mr_solver* h)
     if (h->macro_exec) cudaGraphExecDestroy(h->macro_exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (auto& e : h->ev) cudaEventDestroy(e);
-    for (void* p : h->allocs) cudaFree(p);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->stream); // back to the pool, in stream order
     delete h;
 }
 
