@@ -467,7 +467,27 @@ def run_ours(args):
     torch.cuda.synchronize()
     gts_s = e0.elapsed_time(e1) / 1e3
     gst = gts.stats()
+    u_gts = gts.uniform()
     gts.close()
+
+    # ---- equal accuracy: both adaptive solutions against the finite-volume
+    # solution on the finest grid (eps = 0, global step, no adaptation: every
+    # cell of level L is a leaf), L1 norm as the paper's (mean over the finest
+    # cells), per variable
+    fv = pkg.Solver(p.replace(eps=0.0, time_mode=inputs.TIME_GTS, adapt_mode=inputs.ADAPT_NEVER), qn,
+                    stream=stream)
+    fv.step(args.t_end)
+    u_fv = fv.uniform()
+    fv.close()
+    u_lt = uni_pin.reshape(u_fv.shape)
+    l1 = lambda u: [float(x) for x in np.abs(u - u_fv).reshape(u_fv.shape[0], -1).mean(axis=1)]
+    e_lt, e_gts = l1(u_lt), l1(u_gts)
+    t_lt = tmax / args.steps
+    accuracy = {"reference": "finite volumes on the finest grid (eps = 0, global step)",
+                "l1_lt_nerk": e_lt, "l1_gts": e_gts, "lt_speedup_vs_gts": gts_s / t_lt,
+                # the paper's cost mu = L1 error x time; lambda = mu_GTS / mu_LT > 1
+                # favours MRLT/NERK (density error)
+                "cost_ratio_lambda": (e_gts[0] * gts_s) / (e_lt[0] * t_lt)}
 
     # ---- the same solve in the mixed-precision mode (FP32 face fluxes), and
     # its relative L1 distance from the FP64 result at t_end
@@ -515,6 +535,7 @@ def run_ours(args):
            "gts": {"ms_per_solve": 1e3 * gts_s, "leaf_updates": gst["updates"],
                    "updates_per_s": gst["updates"] / gts_s},
            "lt_speedup_vs_gts": gts_s / (tmax / args.steps),
+           "equal_accuracy": accuracy,
            "precision_mode": mixed,
            "roofline_uniform": uniform}
     if batched is not None:

@@ -147,6 +147,21 @@ def burgers_2d(L: int = 7, eps: float = 1e-2, min_level: int = 2,
     return p, u[None, :, :].copy()
 
 
+def burgers_3d(L: int = 5, eps: float = 1e-2, min_level: int = 2, rk_order: int = 3,
+               time_mode: int = TIME_LT, t_end: float = 0.1, bc: int = BC_PERIODIC) -> tuple[Problem, np.ndarray]:
+    """3D inviscid Burgers u_t + sum_k (u^2/2)_{x_k} = 0 on [0,1]^3 with
+    u0 = sin(2 pi x) sin(2 pi y) sin(2 pi z) (exact cell averages)."""
+    n = 1 << L
+    h = 1.0 / n
+    a = np.arange(n) * h
+    s = (np.cos(2 * np.pi * a) - np.cos(2 * np.pi * (a + h))) / (2 * np.pi * h)
+    u = s[:, None, None] * s[None, :, None] * s[None, None, :]
+    p = Problem(dim=3, equation=EQ_BURGERS, max_level=L, min_level=min_level, eps=eps, eps_mode=0,
+                rk_order=rk_order, time_mode=time_mode, cfl=0.5, bc=(bc,) * 3, t_end=t_end,
+                name=f"burgers3d_L{L}")
+    return p, u[None].copy()
+
+
 def burgers_2d_paper(L: int = 10, eps: float = 1e-3, min_level: int = 3, rk_order: int = 2,
                      time_mode: int = TIME_LT, t_end: float = 0.9) -> tuple[Problem, np.ndarray]:
     """The paper's 2D Burgers case (Sec. 5.1): sin(2 pi x) sin(2 pi y) on

@@ -258,3 +258,11 @@ def test_rd_2d_dirichlet():
     p, q = I.rd_bumps_2d(L=7, eps=1e-3, seed=4)
     gpu, ref = _run_both(p.replace(bc=(I.BC_DIRICHLET0,) * 3), q, t=0.03)
     assert_parity(gpu, ref)
+
+
+@pytest.mark.parametrize("bc", [I.BC_PERIODIC, I.BC_NEUMANN, I.BC_DIRICHLET0])
+def test_burgers_3d_walls(bc):
+    """3D scalar problem: prediction and stencils across walls and corners"""
+    p, q = I.burgers_3d(L=5, eps=1e-2, min_level=2, bc=bc)
+    gpu, ref = _run_both(p, q, t=0.04)
+    assert_parity(gpu, ref)

@@ -63,3 +63,16 @@ def test_dirichlet_2d_eps0_equals_fv(rk):
     # and it differs from the periodic run: the walls matter in 2D
     fvp = R.rk_solve(q[0].copy(), lambda v: R.burgers_rhs_nd(v, 1.0 / n, (0, 0)), dt, 20, rk)
     assert np.abs(fvp - fv).max() > 1e-6
+
+
+def test_dirichlet_3d_eps0_equals_fv():
+    """corner ghosts take the product of the per-direction signs"""
+    L = 4
+    n = 1 << L
+    p, q = I.burgers_3d(L=L, eps=0.0, min_level=2, time_mode=I.TIME_GTS, bc=DIR)
+    o = oracle.Oracle(p, q)
+    dt = 0.3 / n
+    o.iterate(dt, 8)
+    u = o.uniform()[0]
+    fv = R.rk_solve(q[0].copy(), lambda v: R.burgers_rhs_nd(v, 1.0 / n, (DIR, DIR, DIR)), dt, 8, 3)
+    assert np.abs(u - fv).max() <= 1e-12 * np.abs(fv).max()
