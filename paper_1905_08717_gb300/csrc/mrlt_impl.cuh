@@ -112,20 +112,20 @@ struct Ctx {
 
 // Ghost rule, the same on every level: periodic wrap; homogeneous Neumann as
 // an even mirror; zero Dirichlet (scalar equations) as an odd mirror, the
-// ghost taking the negated value: sgn changes sign at every reflection on a
-// Dirichlet wall.
-__device__ __forceinline__ int wrap_or_mirror(const Grid& g, int l, int k, int p, double& sgn)
+// ghost taking the negated value: the parity neg flips at every reflection
+// on a Dirichlet wall (an odd count negates the value).
+__device__ __forceinline__ int wrap_or_mirror(const Grid& g, int l, int k, int p, int& neg)
 {
     const int n = g.n[l];
     if (g.bc[k] == 0) {
         p %= n;
         return p < 0 ? p + n : p;
     }
-    const bool odd = g.bc[k] == 2;
+    const int odd = g.bc[k] == 2;
 #pragma unroll 1
     for (int it = 0; it < 8 && (p < 0 || p >= n); ++it) {
         p = p < 0 ? -1 - p : 2 * n - 1 - p;
-        if (odd) sgn = -sgn;
+        neg ^= odd;
     }
     return p < 0 ? 0 : (p >= n ? n - 1 : p);
 }
@@ -301,18 +301,18 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
     // site cost far more compile time than the loop overhead they save
 #pragma unroll(D > 2 ? 1 : 3)
     for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
-        double sz = 1.0;
-        const int z = D > 2 ? wrap_or_mirror(g, pl, 2, P2 + dz, sz) : 0;
+        int nz = 0;
+        const int z = D > 2 ? wrap_or_mirror(g, pl, 2, P2 + dz, nz) : 0;
         const double wz = D > 2 ? pw(a2, dz) : 1.0;
 #pragma unroll(D > 2 ? 1 : 3)
         for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
-            double syz = sz;
-            const int y = D > 1 ? wrap_or_mirror(g, pl, 1, P1 + dy, syz) : 0;
+            int nyz = nz;
+            const int y = D > 1 ? wrap_or_mirror(g, pl, 1, P1 + dy, nyz) : 0;
             const double wyz = wz * (D > 1 ? pw(a1, dy) : 1.0);
 #pragma unroll
             for (int dxx = -1; dxx <= 1; ++dxx) {
-                double sgn = syz;
-                const int xx = wrap_or_mirror(g, pl, 0, P0 + dxx, sgn);
+                int neg = nyz;
+                const int xx = wrap_or_mirror(g, pl, 0, P0 + dxx, neg);
                 const long long id = cell_id(g, pl, xx, y, z);
                 const int st = status(g, pl, id);
                 if (st == 0) {
@@ -321,7 +321,8 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
                 }
                 double val[M];
                 expose<M>(g, x, pl, id, st, val);
-                const double w = (wyz * pw(a0, dxx)) * sgn; // sgn = -1 for an odd-mirror ghost
+                const double w0 = wyz * pw(a0, dxx);
+                const double w = neg ? -w0 : w0; // an odd-mirror ghost enters negated
 #pragma unroll
                 for (int v = 0; v < M; ++v) out[v] += w * val[v];
             }
@@ -334,14 +335,14 @@ template <int D, int M>
 __device__ __forceinline__ void value_at(const Grid& g, const Ctx& x, int l, const int p[3], double* out)
 {
     int q[3] = {0, 0, 0};
-    double sgn = 1.0;
+    int neg = 0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) q[k] = wrap_or_mirror(g, l, k, p[k], sgn);
+    for (int k = 0; k < D; ++k) q[k] = wrap_or_mirror(g, l, k, p[k], neg);
     const long long id = cell_id(g, l, q[0], q[1], q[2]);
     const int st = status(g, l, id);
     if (st) expose<M>(g, x, l, id, st, out);
     else predict<D, M>(g, x, l, q, out);
-    if (sgn < 0.0) {
+    if (neg) {
 #pragma unroll
         for (int v = 0; v < M; ++v) out[v] = -out[v];
     }

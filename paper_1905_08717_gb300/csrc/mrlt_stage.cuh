@@ -15,11 +15,13 @@ namespace mrlt {
 //   s = 1: q*  = q^n + dt_l f
 //   s = 2: RK2 q^{n+1} = q^n/2 + q*/2 + dt_l f/2 ; RK3 q** = 3q^n/4 + q*/4 + dt_l f/4
 //   s = 3: q^{n+1} = q^n/3 + 2q**/3 + 2 dt_l f/3
+// qs is the leaf's own value at stage s (q^n, q*, q** for s = 1, 2, 3: its
+// exposure, already staged in shared memory) and q0 its q^n (s >= 2).
 template <int M>
-__device__ __forceinline__ void rk_update(const Grid& g, int u, long long id, int s, double dtl, const double* f)
+__device__ __forceinline__ void rk_update(const Grid& g, int u, long long id, int s, double dtl, const double* f,
+                                          const double* q0, const double* qs)
 {
     const long long N = g.N[u];
-    double* q0 = fbase_w(g, F_Q0, u) + id;
     double* q1 = fbase_w(g, F_Q1, u) + id;
     double* q2 = fbase_w(g, F_Q2, u) + id;
     double* qe = fbase_w(g, F_QE, u) + id;
@@ -27,12 +29,12 @@ __device__ __forceinline__ void rk_update(const Grid& g, int u, long long id, in
     for (int v = 0; v < M; ++v) {
         const double kk = dtl * f[v];
         if (s == 1) {
-            q1[v * N] = q0[v * N] + kk;
+            q1[v * N] = qs[v] + kk;
         } else if (s == 2) {
-            if (g.rk == 2) qe[v * N] = 0.5 * q0[v * N] + 0.5 * q1[v * N] + 0.5 * kk;
-            else q2[v * N] = 0.75 * q0[v * N] + 0.25 * q1[v * N] + 0.25 * kk;
+            if (g.rk == 2) qe[v * N] = 0.5 * q0[v] + 0.5 * qs[v] + 0.5 * kk;
+            else q2[v * N] = 0.75 * q0[v] + 0.25 * qs[v] + 0.25 * kk;
         } else {
-            qe[v * N] = (1.0 / 3.0) * q0[v * N] + (2.0 / 3.0) * q2[v * N] + (2.0 / 3.0) * kk;
+            qe[v * N] = (1.0 / 3.0) * q0[v] + (2.0 / 3.0) * qs[v] + (2.0 / 3.0) * kk;
         }
     }
 }
@@ -398,9 +400,18 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
         const int b = bz * SZ + by * SY + bx;
         if (tile_leaf(bx, by, bz)) {
         const long long id = cell_id(g, u, ox + i, oy + j, oz + kz);
-        double self[M], f[M];
+        double self[M], f[M], q0p[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) self[v] = sW[v][b];
+        if (s >= 2) { // q^n (the stage value itself is the staged exposure)
+            const long long N = g.N[u];
+            const double* q0 = fbase(g, F_Q0, u) + id;
+#pragma unroll
+            for (int v = 0; v < M; ++v) q0p[v] = q0[v * N];
+        } else {
+#pragma unroll
+            for (int v = 0; v < M; ++v) q0p[v] = self[v];
+        }
         source<EQ, M>(g, self, f);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -434,7 +445,7 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
                 reg_add<M>(g, u, id, 2 * k + 1, kp, bw, Fp);
             }
         }
-        rk_update<M>(g, u, id, s, dtl, f);
+        rk_update<M>(g, u, id, s, dtl, f, q0p, self);
         }
     }
     __syncthreads(); // shared arrays are reused by the next tile

@@ -725,12 +725,12 @@ __global__ void k_uni_down(Grid g, int l, double* T, uint8_t* us)
             double acc = 0.0;
             FOR3(D, dx, dy, dz)
             {
-                double sgn = 1.0;
-                const int x = wrap_or_mirror(g, l - 1, 0, P[0] + dx, sgn);
-                const int y = D > 1 ? wrap_or_mirror(g, l - 1, 1, P[1] + dy, sgn) : 0;
-                const int z = D > 2 ? wrap_or_mirror(g, l - 1, 2, P[2] + dz, sgn) : 0;
-                const double w = (pw(c[0] & 1, dx) * (D > 1 ? pw(c[1] & 1, dy) : 1.0) *
-                                  (D > 2 ? pw(c[2] & 1, dz) : 1.0)) * sgn;
+                int neg = 0;
+                const int x = wrap_or_mirror(g, l - 1, 0, P[0] + dx, neg);
+                const int y = D > 1 ? wrap_or_mirror(g, l - 1, 1, P[1] + dy, neg) : 0;
+                const int z = D > 2 ? wrap_or_mirror(g, l - 1, 2, P[2] + dz, neg) : 0;
+                const double w0 = pw(c[0] & 1, dx) * (D > 1 ? pw(c[1] & 1, dy) : 1.0) * (D > 2 ? pw(c[2] & 1, dz) : 1.0);
+                const double w = neg ? -w0 : w0;
                 acc += w * Tp[v * Np + cell_id(g, l - 1, x, y, z)];
             }
             Tl[v * N + id] = acc;
