@@ -137,6 +137,17 @@ mr_status mr_step(mr_solver* h, double t_target, long long* iters_out);
  * May stop inside a macro step; dt may change only at a macro-step boundary. */
 mr_status mr_iterate(mr_solver* h, double dt, long long n_iters, long long* iters_out);
 
+/* Asynchronous mode (enable = 1): mr_iterate and mr_step return once their
+ * work is enqueued on the solver's stream instead of after it has completed
+ * (mr_step still waits for each macro step's CFL value, which sets its step).
+ * Errors found on the device, including the non-finite check after every
+ * macro step, are reported by the next mr_sync (or by mr_set_async(h, 0),
+ * which synchronises).  MR_E_STATE for an instance of a batch or server. */
+mr_status mr_set_async(mr_solver* h, int enable);
+
+/* Wait for all work of the solver and report any error it found. */
+mr_status mr_sync(mr_solver* h);
+
 /* What mr_read returns. */
 enum {
     MR_READ_LEAF_KEYS = 0,   /* int32 [n_leaves][4]: level, i, j, k (ordered by
@@ -202,6 +213,14 @@ const char* mr_last_error(const mr_solver* h);
 
 /* Number of kernel launches issued by this handle since creation. */
 long long mr_launch_count(const mr_solver* h);
+
+/* Device memory of solvers comes from a library pool per device that keeps
+ * freed memory reserved for the next solver (so that creating and destroying
+ * solvers never synchronises the device).  This returns the reserved memory
+ * that no live solver uses to the device, e.g. before handing the GPU's
+ * memory to another allocator.  Memory that destroyed solvers' pending work
+ * still uses is released once that work has completed. */
+mr_status mr_release_cached_memory(void);
 
 /* ---- Batched instances --------------------------------------------------
  * Many independent problems (each its own configuration, level range and

@@ -67,6 +67,10 @@ def library() -> ctypes.CDLL:
         lib.mr_profile.restype = ctypes.c_int
         lib.mr_launch_count.argtypes = [vp]
         lib.mr_launch_count.restype = ll
+        lib.mr_set_async.argtypes = [vp, ctypes.c_int]
+        lib.mr_sync.argtypes = [vp]
+        lib.mr_release_cached_memory.argtypes = []
+        lib.mr_release_cached_memory.restype = ctypes.c_int
         lib.mr_leaf_mass_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double), vp, vp, ll, ctypes.c_int,
                                              vp, vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -98,7 +102,7 @@ def library() -> ctypes.CDLL:
         lib.mr_server_destroy.argtypes = [vp]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
                      "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create", "mr_create_from_state",
-                     "mr_batch_step", "mr_server_create", "mr_server_submit", "mr_server_advance",
+                     "mr_batch_step", "mr_set_async", "mr_sync", "mr_server_create", "mr_server_submit", "mr_server_advance",
                      "mr_server_poll", "mr_server_status", "mr_server_release"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -141,6 +145,13 @@ def leaf_mass_noalloc(dim: int, lo, hi, keys_ptr: int, values_ptr: int, n_leaves
                                  ctypes.c_void_p(_stream_handle(stream)), msg, len(msg))
     if r != 0:
         raise MRError(r, msg.value.decode())
+
+
+def release_cached_memory() -> None:
+    """Return the device memory the library keeps cached for future solvers."""
+    r = library().mr_release_cached_memory()
+    if r != 0:
+        raise MRError(r, "mr_release_cached_memory failed")
 
 
 def _dptr(a: np.ndarray):
@@ -236,6 +247,14 @@ class Solver:
         it = ctypes.c_longlong()
         self._check(library().mr_iterate(self._h, dt, n_iters, ctypes.byref(it)), "iterate")
         return it.value
+
+    def set_async(self, enable: bool):
+        """step()/iterate() return once their work is enqueued; errors are
+        reported by sync()"""
+        self._check(library().mr_set_async(self._h, int(enable)), "set_async")
+
+    def sync(self):
+        self._check(library().mr_sync(self._h), "sync")
 
     def _read(self, what, dtype, shape=None, out=None):
         lib = library()

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 #include <chrono>
+#include <mutex>
 #include <thread>
 
 using namespace mrlt;
@@ -49,6 +50,10 @@ struct mr_solver {
     // batched use: the macro-step finiteness check copies the device error
     // bits here (pinned host memory) instead of synchronising
     int* async_err = nullptr;
+    // mr_set_async: calls return without waiting; own_err is the solver's own
+    // pinned slot for async_err (batches and servers use theirs)
+    bool async = false;
+    int* own_err = nullptr;
     // device bytes requested by dev_alloc; with dry set nothing is allocated
     // (the footprint of a configuration is projected without creating it)
     size_t bytes = 0;
@@ -106,11 +111,13 @@ mr_status validate(const mr_config* c)
 // process exits.
 constexpr int kMaxPoolDevices = 64;
 cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+std::mutex g_pool_mutex; // pools are created once per device, also under concurrent first use
 
 cudaMemPool_t device_pool()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
     if (!g_pool[dev]) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -773,19 +780,55 @@ mr_status mr_step(mr_solver* h, double t_target, long long* iters_out)
         h->t = last ? t_target : t0 + nit * dt;
     }
     if (iters_out) *iters_out = h->iters - it0;
-    return sync_check(h);
+    return h->async ? MR_OK : sync_check(h);
 }
 
 mr_status mr_iterate(mr_solver* h, double dt, long long n, long long* iters_out)
 {
     if (!h || !(dt > 0.0) || n < 0) return MR_E_INVALID;
-    const long long it0 = h->iters;
-    for (long long i = 0; i < n; ++i) {
-        MR_TRY(run_iters(h, dt, 1));
-        h->t += dt;
+    const long long it0 = h->iters, nit = 1LL << (h->K.g.L - h->K.g.lb);
+    long long i = 0;
+    while (i < n) { // whole macro steps at once (a graph), single iterations otherwise
+        const long long chunk = (h->pos == 0 && n - i >= nit) ? nit : 1;
+        MR_TRY(run_iters(h, dt, chunk));
+        for (long long k = 0; k < chunk; ++k) h->t += dt;
+        i += chunk;
     }
     if (iters_out) *iters_out = h->iters - it0;
-    return sync_check(h);
+    return h->async ? MR_OK : sync_check(h);
+}
+
+mr_status mr_set_async(mr_solver* h, int enable)
+{
+    if (!h) return MR_E_INVALID;
+    if (h->async_err && h->async_err != h->own_err) return MR_E_STATE; // a batch or server instance
+    if (enable) {
+        if (!h->own_err) {
+            if (cudaMallocHost((void**)&h->own_err, sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                return MR_E_NOMEM;
+            }
+            *h->own_err = 0;
+        }
+        h->async_err = h->own_err;
+        h->async = true;
+        return MR_OK;
+    }
+    const mr_status r = mr_sync(h);
+    h->async = false;
+    h->async_err = nullptr;
+    return r;
+}
+
+mr_status mr_sync(mr_solver* h)
+{
+    if (!h) return MR_E_INVALID;
+    MR_TRY(sync_check(h));
+    if (h->async_err && *h->async_err) {
+        h->err = "non-finite value found by a macro-step check";
+        return MR_E_NUMERIC;
+    }
+    return MR_OK;
 }
 
 mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
@@ -901,6 +944,10 @@ void mr_destroy(mr_solver* h)
 {
     if (!h) return;
     if (h->macro_exec) cudaGraphExecDestroy(h->macro_exec);
+    if (h->own_err) {
+        cudaStreamSynchronize(h->stream); // the slot may still receive a pending copy
+        cudaFreeHost(h->own_err);
+    }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (auto& e : h->ev) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFreeAsync(p, h->stream); // back to the pool, in stream order
@@ -910,6 +957,17 @@ void mr_destroy(mr_solver* h)
 const char* mr_last_error(const mr_solver* h) { return h ? h->err.c_str() : kNullErr; }
 
 long long mr_launch_count(const mr_solver* h) { return h ? h->K.n + h->stage_launches : 0; }
+
+mr_status mr_release_cached_memory(void)
+{
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    for (int dev = 0; dev < kMaxPoolDevices; ++dev)
+        if (g_pool[dev] && cudaMemPoolTrimTo(g_pool[dev], 0) != cudaSuccess) {
+            cudaGetLastError();
+            return MR_E_CUDA;
+        }
+    return MR_OK;
+}
 
 } // extern "C"
 

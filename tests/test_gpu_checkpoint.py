@@ -67,3 +67,22 @@ def test_invalid_states_are_rejected():
     with pytest.raises(pkg.MRError) as e:  # overlapping leaves
         pkg.Solver.from_state(p, dup, np.concatenate([vals, vals[:1]]), t, iters)
     assert e.value.status == 1
+
+
+def test_async_calls_give_the_same_result():
+    """mr_set_async: step/iterate return once enqueued; mr_sync reports errors"""
+    import paper_1905_08717_gb300 as pkg
+    p, q = I.euler_2d_quadrants(L=7, eps=1e-3, seed=1)
+    a, b = pkg.Solver(p, q), pkg.Solver(p, q)
+    b.set_async(True)
+    dt = 0.5 / 128 / 3.7
+    for s in (a, b):
+        s.iterate(dt, 16)   # one whole macro step (graph) ...
+        s.iterate(dt, 5)    # ... and single iterations
+        s.iterate(dt, 11)
+        s.step(0.08)
+    b.sync()
+    ka, va = a.leaves()
+    kb, vb = b.leaves()
+    assert np.array_equal(ka, kb) and np.array_equal(va, vb)
+    b.set_async(False)

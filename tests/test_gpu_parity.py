@@ -266,3 +266,19 @@ def test_burgers_3d_walls(bc):
     p, q = I.burgers_3d(L=5, eps=1e-2, min_level=2, bc=bc)
     gpu, ref = _run_both(p, q, t=0.04)
     assert_parity(gpu, ref)
+
+
+def test_release_cached_memory_returns_device_memory():
+    """destroyed solvers' memory stays cached in the library's pool until
+    released back to the device"""
+    import torch
+    import paper_1905_08717_gb300 as pkg
+    p, q = I.euler_2d_quadrants(L=10, eps=1e-3)
+    s = pkg.Solver(p, q)
+    s.close()
+    torch.cuda.synchronize()
+    free_cached, _ = torch.cuda.mem_get_info()
+    pkg.release_cached_memory()
+    torch.cuda.synchronize()
+    free_released, _ = torch.cuda.mem_get_info()
+    assert free_released - free_cached > 200 << 20  # the solver holds about 0.8 GB
