@@ -190,6 +190,47 @@ def _uniform_roofline(pkg, inputs, torch, peak: float, iters: int = 20) -> dict:
     return out
 
 
+def _timed_solve(pkg, torch, p, q, t_end):
+    s = pkg.Solver(p, q)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step(t_end)
+    e1.record()
+    torch.cuda.synchronize()
+    out = (e0.elapsed_time(e1) / 1e3, s.uniform(), s.stats()["leaves"])
+    s.close()
+    return out
+
+
+def _paper_burgers2d(pkg, inputs, torch, L: int = 10) -> dict:
+    """The paper's 2D Burgers experiment (Sec. 5.1: sin 2 pi x sin 2 pi y, u = 0
+    on the walls, sigma = 0.5, eps = 1e-2, t_f = 0.9) on this GPU: L1 error
+    against the finite-volume solution on the same finest grid, time in % of
+    that finite-volume run, memory (leaves) in % of its cells, and the paper's
+    gain lambda = mu_MR / mu_MRLT, mu = error x time, for RK2 and RK3.  The
+    paper's own figures (its CPU, AUSM+ flux) are quoted beside as context."""
+    import numpy as np
+    paper = {2: {"mr": (1.2890e-2, 14.7, 4.1), "lt": (1.0740e-2, 6.7, 4.4), "lambda": 2.63},
+             3: {"mr": (1.2893e-2, 15.3, 4.1), "lt": (1.0699e-2, 6.4, 4.4), "lambda": 2.88}}
+    out = {"workload": f"paper 2D Burgers, L={L}, eps=1e-2, sigma=0.5, t=0.9, zero-Dirichlet walls"}
+    for rk in (2, 3):
+        p, q = inputs.burgers_2d_paper(L=L, eps=1e-2, min_level=3, rk_order=rk)
+        t_fv, u_fv, n_fv = _timed_solve(pkg, torch, p.replace(eps=0.0, time_mode=inputs.TIME_GTS,
+                                                               adapt_mode=inputs.ADAPT_NEVER), q, 0.9)
+        row = {"fv_s": t_fv}
+        for key, mode in (("mr", inputs.TIME_GTS), ("lt", inputs.TIME_LT)):
+            t, u, leaves = _timed_solve(pkg, torch, p.replace(time_mode=mode), q, 0.9)
+            row[key] = {"l1": float(np.abs(u - u_fv).mean()), "time_pct_fv": 100.0 * t / t_fv,
+                        "memory_pct_fv": 100.0 * leaves / n_fv, "s": t}
+        row["lambda"] = (row["mr"]["l1"] * row["mr"]["s"]) / (row["lt"]["l1"] * row["lt"]["s"])
+        row["paper"] = {"mr": dict(zip(("l1", "time_pct_fv", "memory_pct_fv"), paper[rk]["mr"])),
+                        "lt": dict(zip(("l1", "time_pct_fv", "memory_pct_fv"), paper[rk]["lt"])),
+                        "lambda": paper[rk]["lambda"]}
+        out[f"rk{rk}"] = row
+    return out
+
+
 def _batched(pkg, inputs, torch, n: int = 256, t1: float = 0.005, span: float = 0.02) -> dict:
     """Batched instances: n 2D reaction-diffusion problems of uneven size (L
     ~ U{7..10}, eps in {1e-3, 1e-4}, RK2 LT/NERK) advanced from t1 to
@@ -515,6 +556,7 @@ def run_ours(args):
              "arithmetic": "FP32 reconstruction + face fluxes; FP64 state, RK update, registers, adaptation"}
 
     uniform = _uniform_roofline(pkg, inputs, torch, peak)
+    paper_b2d = _paper_burgers2d(pkg, inputs, torch) if not args.no_batch else None
     batched = _batched(pkg, inputs, torch) if not args.no_batch else None
     serving = _serving(pkg, inputs, torch) if not args.no_batch else None
 
@@ -542,6 +584,8 @@ def run_ours(args):
         out["batched"] = batched
     if serving is not None:
         out["serving"] = serving
+    if paper_b2d is not None:
+        out["paper_burgers2d"] = paper_b2d
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = _cpu_baseline()
     print(json.dumps(out), flush=True)
