@@ -148,6 +148,15 @@ mr_status mr_set_async(mr_solver* h, int enable);
 /* Wait for all work of the solver and report any error it found. */
 mr_status mr_sync(mr_solver* h);
 
+/* Launch shape: at most `ctas` thread blocks per stage-kernel launch (0, the
+ * default: the device's resident capacity for the kernel, which fills every
+ * SM).  The blocks stride over the active tiles and each cell is written by
+ * one thread, so the results are bitwise the same for every value; a smaller
+ * grid leaves SMs to concurrent solvers (batches, servers).  Waits for the
+ * solver's stream if a captured macro step must be replaced.  MR_E_INVALID
+ * for ctas < 0. */
+mr_status mr_set_grid_cap(mr_solver* h, int ctas);
+
 /* What mr_read returns. */
 enum {
     MR_READ_LEAF_KEYS = 0,   /* int32 [n_leaves][4]: level, i, j, k (ordered by
@@ -249,6 +258,11 @@ mr_status mr_batch_create(int n, const mr_config* cfgs, const double* const* q0s
  * receives the fine iterations done, summed over instances.  On an error the
  * failing instance is reported by mr_batch_last_error. */
 mr_status mr_batch_step(mr_batch* b, double t_target, long long* iters_out);
+
+/* mr_set_grid_cap on every instance: the stage-kernel launches of each
+ * instance use at most `ctas` thread blocks, so that more instances run on the
+ * GPU at once.  Results are unchanged.  Call between steps. */
+mr_status mr_batch_set_grid_cap(mr_batch* b, int ctas);
 
 /* Instance i (0 <= i < n), owned by the batch: use it with mr_read,
  * mr_last_error and mr_launch_count; NULL if i is out of range.  Do not destroy

@@ -69,6 +69,8 @@ def library() -> ctypes.CDLL:
         lib.mr_launch_count.restype = ll
         lib.mr_set_async.argtypes = [vp, ctypes.c_int]
         lib.mr_sync.argtypes = [vp]
+        lib.mr_set_grid_cap.argtypes = [vp, ctypes.c_int]
+        lib.mr_batch_set_grid_cap.argtypes = [vp, ctypes.c_int]
         lib.mr_release_cached_memory.argtypes = []
         lib.mr_release_cached_memory.restype = ctypes.c_int
         lib.mr_leaf_mass_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -102,7 +104,8 @@ def library() -> ctypes.CDLL:
         lib.mr_server_destroy.argtypes = [vp]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
                      "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create", "mr_create_from_state",
-                     "mr_batch_step", "mr_set_async", "mr_sync", "mr_server_create", "mr_server_submit", "mr_server_advance",
+                     "mr_batch_step", "mr_set_async", "mr_sync", "mr_set_grid_cap", "mr_batch_set_grid_cap",
+                     "mr_server_create", "mr_server_submit", "mr_server_advance",
                      "mr_server_poll", "mr_server_status", "mr_server_release"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -256,6 +259,11 @@ class Solver:
     def sync(self):
         self._check(library().mr_sync(self._h), "sync")
 
+    def set_grid_cap(self, ctas: int):
+        """at most `ctas` thread blocks per stage-kernel launch (0: fill the
+        GPU); the results do not depend on it"""
+        self._check(library().mr_set_grid_cap(self._h, int(ctas)), "set_grid_cap")
+
     def _read(self, what, dtype, shape=None, out=None):
         lib = library()
         used = ctypes.c_size_t()
@@ -304,7 +312,7 @@ class Batch:
     instance is a solver with its own stream and its macro step as a CUDA
     graph, so the instances run concurrently on the GPU."""
 
-    def __init__(self, problems, q0s, stream=None):
+    def __init__(self, problems, q0s, stream=None, grid_cap: int = 0):
         lib = library()
         if len(problems) != len(q0s) or not problems:
             raise ValueError("one initial condition per problem, at least one problem")
@@ -322,6 +330,17 @@ class Batch:
             raise MRError(r, f"mr_batch_create failed (instance {bad.value})")
         self.instances = [Solver._view(p, lib.mr_batch_instance(self._b, i), self)
                           for i, p in enumerate(problems)]
+        if grid_cap:
+            self.set_grid_cap(grid_cap)
+
+    def set_grid_cap(self, ctas: int):
+        """at most `ctas` thread blocks per stage-kernel launch of every
+        instance, so that more instances share the GPU at once (0: each launch
+        may fill the GPU); the results do not depend on it"""
+        lib = library()
+        r = lib.mr_batch_set_grid_cap(self._b, int(ctas))
+        if r != 0:
+            raise MRError(r, "batch grid cap: " + lib.mr_batch_last_error(self._b).decode())
 
     def step(self, t_target: float) -> int:
         lib = library()

@@ -497,6 +497,7 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     g.prec = cfg->precision;
     g.flux = cfg->flux;
     g.igm = cfg->equation == MR_EQ_EULER ? 1.0 / (cfg->phys[0] - 1.0) : 0.0;
+    g.gcap = 0;
     long long off = 0, toff = 0;
     for (int l = g.lb; l <= g.L; ++l) {
         g.toff[l] = toff;
@@ -818,6 +819,21 @@ mr_status mr_set_async(mr_solver* h, int enable)
     h->async = false;
     h->async_err = nullptr;
     return r;
+}
+
+mr_status mr_set_grid_cap(mr_solver* h, int ctas)
+{
+    if (!h || ctas < 0) return MR_E_INVALID;
+    if (h->K.g.gcap == ctas) return MR_OK;
+    // a captured macro step holds the old launch shape: drop it once the
+    // stream has passed it, and capture again at the next macro step
+    if (h->macro_exec) {
+        MR_CK(cudaStreamSynchronize(h->stream));
+        MR_CK(cudaGraphExecDestroy(h->macro_exec));
+        h->macro_exec = nullptr;
+    }
+    h->K.g.gcap = ctas;
+    return MR_OK;
 }
 
 mr_status mr_sync(mr_solver* h)
@@ -1159,6 +1175,16 @@ mr_status mr_batch_step(mr_batch* b, double t_target, long long* iters_out)
         it1 += h->iters;
     }
     if (iters_out) *iters_out = it1 - it0;
+    return MR_OK;
+}
+
+mr_status mr_batch_set_grid_cap(mr_batch* b, int ctas)
+{
+    if (!b || ctas < 0) return MR_E_INVALID;
+    for (int i = 0; i < (int)b->inst.size(); ++i) {
+        const mr_status r = mr_set_grid_cap(b->inst[i], ctas);
+        if (r != MR_OK) return batch_fail(b, i, r);
+    }
     return MR_OK;
 }
 

@@ -72,6 +72,7 @@ struct Grid {
     int prec;                       // 0 FP64, 1 mixed: face fluxes in FP32
     int flux;                       // Euler: 0 HLL, 1 AUSM+
     double igm;                     // Euler: 1 / (gamma - 1)
+    int gcap;                       // CTAs per stage launch at most (0: resident capacity)
 };
 
 // Programmatic dependent launch (sm_90 and later).  Every kernel starts by

@@ -460,7 +460,10 @@ static inline int grid_for(const Grid& g, int l)
 
 // One launch of the tiled stage kernel over the active tiles of levels lo..hi;
 // the persistent grid is the device's resident capacity for this instantiation
-// (occupancy API, once per device), capped by the tile count.
+// (occupancy API, once per device), capped by the tile count and by g.gcap
+// when that is set.  CTAs stride over the tile slots and every cell's update
+// and flux registers are written by one thread, so the result does not depend
+// on the grid size.
 template <int EQ, int D, class R>
 static int stage_dispatch(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg)
 {
@@ -483,7 +486,9 @@ static int stage_dispatch(const Grid& g, cudaStream_t st, int lo, int hi, int s,
     if (lo > hi) return 0; // set-up only
     long long total = 0;
     for (int l = lo; l <= hi; ++l) total += (long long)g.ntx[l] * g.nty[l] * g.ntz[l];
-    const long long grid = total < resident[dev] ? total : resident[dev];
+    long long grid = total < resident[dev] ? total : resident[dev];
+    if (g.gcap > 0 && grid > g.gcap) grid = g.gcap;
+    if (grid < 1) grid = 1;
     // launched without a programmatic dependency: the persistent grid assigns
     // tiles statically, so it must find the SMs free to be resident at once
     k_stage_tile<EQ, D, R><<<(unsigned)grid, S::NT, S::SMEM, st>>>(g, lo, hi, s, lmin, b, reg);

@@ -99,3 +99,51 @@ def test_batch_rejects_bad_instance():
     probs[1] = probs[1].replace(rk_order=4)
     with pytest.raises(pkg.MRError, match="instance 1"):
         pkg.Batch(probs, qs)
+
+
+def test_grid_cap_does_not_change_results():
+    """A stage launch of 1, 7 or 152 thread blocks (or the resident capacity)
+    computes bitwise the same leaves, also when the cap changes between macro
+    steps (the captured macro-step graph is replaced)."""
+    import paper_1905_08717_gb300 as pkg
+    probs, qs = _mixed_problems()
+    for i in (4, 5, 6, 7):
+        p, q = probs[i], qs[i]
+        ref = pkg.Solver(p, q)
+        ref.step(0.02)
+        ref.step(0.04)
+        kr, vr = ref.leaves()
+        for caps in ((1, 1), (7, 7), (152, 152), (0, 3), (5, 0)):
+            s = pkg.Solver(p, q)
+            s.set_grid_cap(caps[0])
+            s.step(0.02)
+            s.set_grid_cap(caps[1])
+            s.step(0.04)
+            k, v = s.leaves()
+            assert np.array_equal(k, kr), f"{p.name}, caps {caps}: leaf sets differ"
+            assert np.array_equal(v, vr), f"{p.name}, caps {caps}: values differ"
+            s.close()
+        with pytest.raises(pkg.MRError):
+            ref.set_grid_cap(-1)
+        ref.close()
+
+
+def test_autotuned_batch_equals_default():
+    """The package's tuner picks a cap by timing; whichever it picks, the
+    batch gives bitwise the default batch's results."""
+    import paper_1905_08717_gb300 as pkg
+    from paper_1905_08717_gb300 import autotune
+    probs, qs = _mixed_problems()
+    tune = autotune.tune_batch(probs, qs, 0.01, 0.01, caps=[0, 16, 4])
+    assert tune["best"] in (0, 16, 4) and set(tune["seconds"]) == {0, 16, 4}
+    assert all(v > 0 for v in tune["seconds"].values())
+    b0 = pkg.Batch(probs, qs)
+    bt = pkg.Batch(probs, qs, grid_cap=4)
+    for b in (b0, bt):
+        b.step(0.02)
+    for i in range(len(probs)):
+        k0, v0 = b0.instances[i].leaves()
+        kt, vt = bt.instances[i].leaves()
+        assert np.array_equal(k0, kt) and np.array_equal(v0, vt), f"instance {i}"
+    b0.close()
+    bt.close()
