@@ -317,12 +317,13 @@ def _batched(pkg, inputs, torch, n: int = 256, t1: float = 0.005, span: float = 
             "timing": "host wall clock around synchronous calls"}
 
 
-def _serve(pkg, torch, reqs) -> dict:
+def _serve(pkg, torch, reqs, grid_cap: int = 0) -> dict:
     """Replay (arrival_s, problem, q0, t_end) requests against a fresh
     mr_server in real time (host clock); latency = completion seen by poll -
-    arrival."""
+    arrival.  grid_cap: stage-launch block cap of every request (0: default)."""
     n = len(reqs)
     srv = pkg.Server(mem_budget_bytes=64 << 30, max_active=96)
+    srv.set_grid_cap(grid_cap)
     arrival, done_at, updates = {}, {}, 0
     k = 0
     torch.cuda.synchronize()
@@ -360,16 +361,24 @@ def _serving(pkg, inputs, torch, n: int = 200, rate: float = 200.0) -> dict:
     configured rate when the GPU can sustain it."""
     reqs = inputs.serving_requests(n=n, seed=0, rate=rate)
     sat = _serve(pkg, torch, [(0.0,) + r[1:] for r in reqs])
-    cap = sat["requests_per_s"]
+    # the same capacity run with one stage-kernel block per SM per launch
+    # (the cap the tuner picks for the batched workload); latency is measured
+    # with whichever launch shape gave the higher capacity
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sat_cap = _serve(pkg, torch, [(0.0,) + r[1:] for r in reqs], grid_cap=sms)
+    gcap = sms if sat_cap["requests_per_s"] > sat["requests_per_s"] else 0
+    best = sat_cap if gcap else sat
+    cap = best["requests_per_s"]
     rng = __import__("numpy").random.default_rng(1)
     arr = list(__import__("itertools").accumulate(rng.exponential(1.0 / (0.5 * cap), n)))
-    half = _serve(pkg, torch, [(a,) + r[1:] for a, r in zip(arr, reqs)])
+    half = _serve(pkg, torch, [(a,) + r[1:] for a, r in zip(arr, reqs)], grid_cap=gcap)
     out = {"workload": f"{n} requests: 1D Burgers L10-14 (32-128 fine steps), 2D RD L8-10 (16-64), "
                        "3D blast L6-8 (8-24); eps log-U[1e-4,1e-2]; mixed precision",
-           "capacity": sat, "at_half_capacity": dict(half, rate_per_s=0.5 * cap),
+           "capacity": best, "capacity_default_launch": sat, "capacity_one_block_per_sm": sat_cap,
+           "grid_cap": gcap, "at_half_capacity": dict(half, rate_per_s=0.5 * cap),
            "configured_rate_per_s": rate, "timing": "host wall clock"}
     if rate <= cap:
-        out["at_configured_rate"] = _serve(pkg, torch, reqs)
+        out["at_configured_rate"] = _serve(pkg, torch, reqs, grid_cap=gcap)
     return out
 
 

@@ -321,6 +321,11 @@ mr_status mr_server_release(mr_server* s, long long id);
 /* Device bytes held by admitted, not yet released requests. */
 size_t mr_server_memory(const mr_server* s);
 
+/* mr_set_grid_cap for every request admitted after this call (requests
+ * already running keep their launch shape).  Results are unchanged.
+ * MR_E_INVALID for ctas < 0. */
+mr_status mr_server_set_grid_cap(mr_server* s, int ctas);
+
 /* Reason for the last failure of a server call. */
 const char* mr_server_last_error(const mr_server* s);
 

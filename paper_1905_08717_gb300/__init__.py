@@ -71,6 +71,7 @@ def library() -> ctypes.CDLL:
         lib.mr_sync.argtypes = [vp]
         lib.mr_set_grid_cap.argtypes = [vp, ctypes.c_int]
         lib.mr_batch_set_grid_cap.argtypes = [vp, ctypes.c_int]
+        lib.mr_server_set_grid_cap.argtypes = [vp, ctypes.c_int]
         lib.mr_release_cached_memory.argtypes = []
         lib.mr_release_cached_memory.restype = ctypes.c_int
         lib.mr_leaf_mass_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -104,7 +105,7 @@ def library() -> ctypes.CDLL:
         lib.mr_server_destroy.argtypes = [vp]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
                      "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create", "mr_create_from_state",
-                     "mr_batch_step", "mr_set_async", "mr_sync", "mr_set_grid_cap", "mr_batch_set_grid_cap",
+                     "mr_batch_step", "mr_set_async", "mr_sync", "mr_set_grid_cap", "mr_batch_set_grid_cap", "mr_server_set_grid_cap",
                      "mr_server_create", "mr_server_submit", "mr_server_advance",
                      "mr_server_poll", "mr_server_status", "mr_server_release"):
             getattr(lib, name).restype = ctypes.c_int
@@ -382,6 +383,12 @@ class Server:
     def _check(self, r: int, what: str):
         if r != 0:
             raise MRError(r, f"{what}: {library().mr_server_last_error(self._s).decode()}")
+
+    def set_grid_cap(self, ctas: int):
+        """at most `ctas` thread blocks per stage-kernel launch for requests
+        admitted from now on (0: each launch may fill the GPU); the results
+        do not depend on it"""
+        self._check(library().mr_server_set_grid_cap(self._s, int(ctas)), "set_grid_cap")
 
     def submit(self, problem, q0, t_end: float) -> int:
         cfg = make_config(problem)

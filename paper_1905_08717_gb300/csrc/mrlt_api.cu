@@ -1233,6 +1233,7 @@ struct mr_server {
     unsigned long long* bits = nullptr; // pinned [max_active]
     int* errs = nullptr;                // pinned [max_active]
     std::vector<int> free_slots;
+    int gcap = 0;                       // stage-launch block cap of admitted solvers
     std::string err;
 };
 
@@ -1297,6 +1298,7 @@ mr_status admit(mr_server* s)
             continue;
         }
         q->h->async_err = &s->errs[q->slot];
+        if (s->gcap) mr_set_grid_cap(q->h, s->gcap); // nothing captured yet: cannot fail
         s->used += q->bytes;
         q->state = q->h->t < q->t_end ? 1 : 2;
         if (q->state == 1) s->active.push_back(q);
@@ -1352,6 +1354,13 @@ mr_status mr_server_create(size_t mem_budget_bytes, int max_active, void* cuda_s
     }
     for (int i = max_active - 1; i >= 0; --i) s->free_slots.push_back(i);
     *out = s;
+    return MR_OK;
+}
+
+mr_status mr_server_set_grid_cap(mr_server* s, int ctas)
+{
+    if (!s || ctas < 0) return MR_E_INVALID;
+    s->gcap = ctas;
     return MR_OK;
 }
 

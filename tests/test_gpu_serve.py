@@ -45,16 +45,21 @@ def _drain(srv, done, seconds=300.0):
     raise AssertionError("server did not drain")
 
 
-def test_serve_results_equal_standalone():
+@pytest.mark.parametrize("caps", [(0, 0), (5, 152)])
+def test_serve_results_equal_standalone(caps):
+    """caps: stage-launch block caps for the first and the later requests
+    (0: the default launch shape); the results must not depend on them"""
     import paper_1905_08717_gb300 as pkg
     probs, qs, ends = _requests()
     srv = pkg.Server(mem_budget_bytes=8 << 30, max_active=16)
+    srv.set_grid_cap(caps[0])
     ids, done = [], []
     for p, q, t in zip(probs[:3], qs[:3], ends[:3]):
         ids.append(srv.submit(p, q, t))
     for _ in range(50):  # later requests join a running set
         srv.advance()
         done.extend(srv.poll())
+    srv.set_grid_cap(caps[1])
     for p, q, t in zip(probs[3:], qs[3:], ends[3:]):
         ids.append(srv.submit(p, q, t))
     _drain(srv, done)
