@@ -400,7 +400,8 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
 }
 
 // CFL step of the finest level: sigma * min(dx_L / max sum_k lambda_k, dx_L^2 / (2 d D))
-// CFL reduction (R13), enqueued: the largest sum of characteristic speeds,
+// (the paper fixes only sigma; the step is held for a whole macro step)
+// CFL reduction, enqueued: the largest sum of characteristic speeds,
 // as a bit pattern, lands in *bits when the stream reaches this point
 mr_status cfl_enqueue(mr_solver* h, unsigned long long* bits)
 {
