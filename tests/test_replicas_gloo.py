@@ -65,3 +65,13 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert r.returncode == 0
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_traffic_figure_comes_from_the_committed_dram_summary():
+    """roofline.traffic is the committed per-leaf-stage DRAM figure times the
+    leaf-stages of one launch; the summary must parse to a positive number
+    below the algorithmic bytes of a leaf-stage (the state is L2-resident)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    tpl = bench._traffic_per_leaf_stage()
+    assert tpl is not None and 0.0 < tpl < max(bench.BYTES_PER_LEAF_STAGE.values())
