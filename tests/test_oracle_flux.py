@@ -131,3 +131,34 @@ def test_ausm_pressure_split_is_twice_differentiable_at_sonic_point():
     r = [(1.0 - P_of(us_star - h)) / h ** 2 for h in (4e-3, 2e-3, 1e-3)]
     # cubic behaviour: the ratio halves with h (a quadratic term would keep it)
     assert r[2] < 0.6 * r[0] + 1e-6, r
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_ausm_plus_resolves_contacts_exactly(d):
+    """Liou's splittings satisfy M+(M) + M-(M) = M and P+(M) + P-(M) = 1 for
+    every Mach number, so across a contact (equal velocity and pressure, any
+    density jump) AUSM+ returns the upwind physical flux exactly, and zero
+    mass flux for a contact at rest.  A splitting whose halves do not sum to
+    M or to 1 (a wrong sign or coefficient in one half) fails this.  HLL
+    smears a contact at rest (mass flux -c (rho_R - rho_L) / 2 for equal
+    sound speeds' bound), which shows that the check discriminates."""
+    rng = np.random.default_rng(40 + d)
+    pa, ph = _problem(d, 1), _problem(d, 0)
+    for _ in range(20):
+        rhoL = rng.uniform(0.2, 1.5)
+        rhoR = rhoL * rng.uniform(1.5, 3.0)
+        pr = rng.uniform(0.1, 5.0)
+        for k in range(d):
+            vel = rng.uniform(-2.5, 2.5, d)  # sub- and supersonic normal speeds
+            for un in (0.0, vel[k], -vel[k]):
+                v = vel.copy()
+                v[k] = un
+                UL, UR = _cons(rhoL, v, pr), _cons(rhoR, v, pr)
+                F = oracle.num_flux(pa, k, np.array([UL, UL, UR, UR]))
+                expect = _phys_flux(UL if un >= 0.0 else UR, k)
+                assert np.allclose(F, expect, rtol=1e-13, atol=1e-13 * (1.0 + np.abs(expect).max()))
+                if un == 0.0:
+                    assert abs(F[0]) < 1e-14
+        rest = np.zeros(d)
+        W = np.array([_cons(rhoL, rest, pr)] * 2 + [_cons(rhoR, rest, pr)] * 2)
+        assert abs(oracle.num_flux(ph, 0, W)[0]) > 0.05 * (rhoR - rhoL)
