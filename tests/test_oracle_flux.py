@@ -4,8 +4,9 @@ fixes a property of the exact flux that a plausible mistake breaks: equal
 states give the physical flux (a wrong splitting sum, a dropped pressure
 term); supersonic states give the upwind physical flux (a wrong sign or
 branch of the Mach splitting); mirror symmetry (a wrong sign on one side);
-and the Sod shock tube converges to the exact Riemann solution (anything that
-makes the scheme inconsistent)."""
+the Sod shock tube converges to the exact Riemann solution (anything that
+makes the scheme inconsistent); and AUSM+ resolves contacts exactly (split
+halves that do not sum to M or to 1)."""
 import numpy as np
 import pytest
 
