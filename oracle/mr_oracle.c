@@ -9,6 +9,13 @@
  * NERK partial sums, Sec. 3 "Compact formulation").  Readings of passages the
  * paper leaves open are marked READING and are listed in the design notes.
  *
+ * Parity unpinned (no test outside this file can fix them):
+ *  - beta = 1/8 in the AUSM+ Mach splitting (ausm_mach): taken as Liou (1996)
+ *    publishes it; the other AUSM+ terms are pinned by the flux tests;
+ *  - the internal-child branches of the stage-2/3 projections (Alg. 4, Eq. 15;
+ *    Alg. 6): implemented as printed, but on a graded tree with radius-2
+ *    stencils no leaf value ever depends on them.
+ *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
  * same source gives the same bits on x86-64 and aarch64).
  */
