@@ -186,3 +186,66 @@ def test_leaf_stencils_are_graded(dim, L, seed):
         hi = [min((a >> 1) * s + 3 * s, n) for a in idx]
         blk = cover[tuple(slice(a, b) for a, b in zip(lo, hi))]
         assert blk.min() >= l - 1
+
+
+def _cover(keys, dim, L):
+    """level of the leaf covering each finest cell; -1 where no leaf does
+    (asserting that no cell is covered twice)"""
+    n = 1 << L
+    cover = np.full((n,) * dim, -1, int)
+    for row in keys:
+        l, idx = int(row[0]), [int(a) for a in row[1:1 + dim]]
+        s = 1 << (L - l)
+        blk = tuple(slice(a * s, (a + 1) * s) for a in reversed(idx))  # arrays are [z][y][x]
+        assert np.all(cover[blk] == -1), "overlapping leaves"
+        cover[blk] = l
+    return cover
+
+
+_LT_CASES = {
+    # name: (problem and data, fine iterations, fine step below the CFL limit)
+    "burgers1d": (lambda: I.burgers_1d(L=8, eps=1e-3, min_level=3), 96, 0.5 / 256),
+    "burgers2d": (lambda: I.burgers_2d(L=6, eps=1e-3, min_level=2), 48, 0.25 / 64),
+    "sod": (lambda: I.euler_1d_sod(L=8, eps=1e-3, min_level=2), 120, 0.25 / 256),
+    "quadrants2d": (lambda: I.euler_2d_quadrants(L=6, eps=1e-3, min_level=2), 64, 0.125 / 64),
+    "advection": (lambda: (lambda pq: (pq[0].replace(eps=1e-4, min_level=2), pq[1]))(
+        I.advection_gaussian_1d(L=8)), 128, 0.5 / 256),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_LT_CASES))
+def test_lt_adaptation_keeps_invariants_every_iteration(case):
+    """Adaptation inside the LT loop (Sec. 4, restricted remesh): after every
+    fine iteration n the leaves still partition the box, neighbouring leaves
+    differ by at most one level (across a periodic wrap too), no leaf below
+    l_min(n) = the coarsest level whose step ends at n has split, merged or
+    appeared, and every prediction source the iteration needs exists (the
+    oracle reports a missing one as an error).  Fronts move through the
+    tree, so it really changes; planted mistakes in the admissibility mask,
+    in the grading closure, or an unrestricted remesh each fail a case."""
+    make, steps, dt = _LT_CASES[case]
+    p, q = make()
+    dim = p.dim
+    p = p.replace(adapt_mode=I.ADAPT_EVERY)
+    L, lb = p.max_level, p.min_level
+    nit = 1 << (L - lb)
+    o = oracle.Oracle(p, q)
+    prev = _cover(o.leaves()[0], dim, L)
+    changed_total = changed_above_base = 0
+    for n in range(steps):
+        pos = n % nit
+        lmin = next(l for l in range(lb, L + 1) if pos % (1 << (L - l)) == 0)
+        o.iterate(dt, 1)
+        cur = _cover(o.leaves()[0], dim, L)
+        assert cur.min() >= lb, "a hole in the partition or a leaf below the base level"
+        for ax in range(dim):
+            assert np.abs(np.diff(cur, axis=ax)).max() <= 1
+            if p.bc[dim - 1 - ax] == I.BC_PERIODIC:  # neighbours across the wrap ([z][y][x] arrays)
+                assert np.abs(cur - np.roll(cur, 1, axis=ax)).max() <= 1
+        low = (np.minimum(prev, cur) < lmin)
+        assert np.array_equal(prev[low], cur[low]), f"iteration {n}: a level below l_min = {lmin} changed"
+        if not np.array_equal(prev, cur):
+            changed_total += 1
+            changed_above_base += lmin > lb
+        prev = cur
+    assert changed_total >= 3 and changed_above_base >= 1
