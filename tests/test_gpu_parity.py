@@ -282,3 +282,33 @@ def test_release_cached_memory_returns_device_memory():
     torch.cuda.synchronize()
     free_released, _ = torch.cuda.mem_get_info()
     assert free_released - free_cached > 200 << 20  # the solver holds about 0.8 GB
+
+
+_MOVING = {
+    # name: (problem and data, fine iterations, fine step below the CFL limit)
+    "sod": (lambda: I.euler_1d_sod(L=8, eps=1e-3, min_level=2), 48, 0.25 / 256),
+    "quadrants2d": (lambda: I.euler_2d_quadrants(L=6, eps=1e-3, min_level=2), 32, 0.125 / 64),
+    "burgers2d": (lambda: I.burgers_2d(L=6, eps=1e-3, min_level=2), 32, 0.25 / 64),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_MOVING))
+def test_every_lt_iteration_matches_oracle(case):
+    """Leaf sets and values agree with the oracle after every single fine
+    iteration of an LT run whose tree moves (restricted remesh at every
+    iteration, stops at every position inside the macro step)."""
+    make, steps, dt = _MOVING[case]
+    p, q = make()
+    p = p.replace(adapt_mode=I.ADAPT_EVERY)
+    gpu, ref = _solver(p, q), oracle.Oracle(p, q)
+    moved = 0
+    prev = ref.leaves()[0]
+    for n in range(steps):
+        gpu.iterate(dt, 1)
+        ref.iterate(dt, 1)
+        assert_parity(gpu, ref, f"{case}, iteration {n}")
+        k = ref.leaves()[0]
+        moved += not np.array_equal(k, prev)
+        prev = k
+    assert moved >= 2
+    gpu.close()
