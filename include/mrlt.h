@@ -154,7 +154,8 @@ mr_status mr_sync(mr_solver* h);
  * one thread, so the results are bitwise the same for every value; a smaller
  * grid leaves SMs to concurrent solvers (batches, servers).  Waits for the
  * solver's stream if a captured macro step must be replaced.  MR_E_INVALID
- * for ctas < 0. */
+ * for a NULL handle or ctas < 0; MR_E_CUDA if that wait fails.  The paper has
+ * no counterpart: it runs one problem on one CPU core. */
 mr_status mr_set_grid_cap(mr_solver* h, int ctas);
 
 /* What mr_read returns. */
@@ -261,7 +262,9 @@ mr_status mr_batch_step(mr_batch* b, double t_target, long long* iters_out);
 
 /* mr_set_grid_cap on every instance: the stage-kernel launches of each
  * instance use at most `ctas` thread blocks, so that more instances run on the
- * GPU at once.  Results are unchanged.  Call between steps. */
+ * GPU at once.  Results are unchanged.  Call between steps.  MR_E_INVALID for
+ * a NULL batch or ctas < 0; otherwise the first failing instance's status,
+ * named by mr_batch_last_error. */
 mr_status mr_batch_set_grid_cap(mr_batch* b, int ctas);
 
 /* Instance i (0 <= i < n), owned by the batch: use it with mr_read,
@@ -323,7 +326,7 @@ size_t mr_server_memory(const mr_server* s);
 
 /* mr_set_grid_cap for every request admitted after this call (requests
  * already running keep their launch shape).  Results are unchanged.
- * MR_E_INVALID for ctas < 0. */
+ * MR_E_INVALID for a NULL server or ctas < 0. */
 mr_status mr_server_set_grid_cap(mr_server* s, int ctas);
 
 /* Reason for the last failure of a server call. */
