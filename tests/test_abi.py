@@ -185,3 +185,37 @@ def test_checkpoint_state_is_checked_on_the_host(lib):
     assert call(two + [[2, 0, 0, 0]]) == 1          # overlapping leaves
     assert call([[0, 0, 0, 0]]) == 1                # a level below min_level
     assert call([[1, 0, 0, 0], [1, 2, 0, 0]]) == 1  # an index outside its level
+
+
+@pytest.mark.parametrize("which", ["library", "oracle"])
+def test_ctypes_config_matches_the_c_struct(tmp_path, which):
+    """The binding's ctypes mirror of the configuration struct has the C
+    compiler's field names, offsets and size (a mismatch would hand the
+    library a silently corrupted configuration)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    if which == "library":
+        import paper_1905_08717_gb300 as pkg
+        cls, header, struct = pkg.mr_config, os.path.join(ROOT, "include", "mrlt.h"), "mr_config"
+    else:
+        import oracle
+        cls, header, struct = oracle._Cfg, os.path.join(ROOT, "oracle", "mr_oracle.h"), "or_config"
+    names = [f[0] for f in cls._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"%s\"\nint main(void){\n"
+                   "printf(\"%%zu\\n\", sizeof(%s));\n%s return 0;}\n" % (
+                       header, struct,
+                       "".join('printf("%%zu\\n", offsetof(%s, %s));\n' % (struct, n) for n in names)))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(cls)
+    assert out[1:] == [getattr(cls, n).offset for n in names]
+    # every field the header declares is mirrored (a trailing field could hide in padding)
+    txt = re.sub(r"/\*.*?\*/", "", open(header).read(), flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\}" % struct, txt, flags=re.S).group(1)
+    declared = [re.sub(r"\[.*?\]", "", n).strip()
+                for decl in re.findall(r"\b(?:int|double)\s+([^;]+);", body) for n in decl.split(",")]
+    assert declared == names
