@@ -1,0 +1,72 @@
+"""Dimensional embedding pins of the oracle: a 2D or 3D run whose data vary
+along one axis only must reproduce the 1D run on every line along that axis,
+with the momentum component of that axis in the 1D momentum's place and the
+others zero.  Fluxes across the other axes are equal on both sides of every
+cell and cancel exactly.  A transposed index, a wrong normal velocity or a
+momentum component swapped between directions fails this."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_08717_gb300 import inputs as I
+
+G = 1.4
+
+
+def _run(p, q, dt, n):
+    o = oracle.Oracle(p, q)
+    o.iterate(dt, n)
+    return o.uniform()
+
+
+def _sod_1d(L):
+    p, q = I.euler_1d_sod(L=L, eps=0.0, min_level=2, rk_order=3, time_mode=I.TIME_GTS)
+    return p.replace(adapt_mode=I.ADAPT_NEVER), q
+
+
+def _embed(q1, d, axis):
+    """1D Euler data (rho, m, E) [3, n] -> d-dim data varying along `axis`
+    (0 = x, 1 = y, 2 = z), arrays indexed [v][z][y][x]"""
+    n = q1.shape[1]
+    out = np.zeros((d + 2,) + (n,) * d)
+    shape = [1] * d
+    shape[d - 1 - axis] = n
+    for v, src in ((0, q1[0]), (1 + axis, q1[1]), (d + 1, q1[2])):
+        out[v] = np.broadcast_to(src.reshape(shape), (n,) * d)
+    return out
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+@pytest.mark.parametrize("d,axis", [(2, 0), (2, 1), (3, 0), (3, 2)])
+def test_euler_along_one_axis_reproduces_1d(d, axis, flux):
+    L = 6 if d == 2 else 4
+    p1, q1 = _sod_1d(L)
+    p1 = p1.replace(flux=flux)
+    # a moving shock tube: add a uniform velocity so that both signs of u occur
+    q1 = q1.copy()
+    q1[2] += 0.5 * 0.3 ** 2 * q1[0]
+    q1[1] = 0.3 * q1[0]
+    dt, n = 0.2 / (1 << L), 12
+    u1 = _run(p1, q1, dt, n)
+    pd = p1.replace(dim=d, bc=(I.BC_NEUMANN,) * 3)
+    ud = _run(pd, _embed(q1, d, axis), dt, n)
+    want = _embed(u1, d, axis)
+    assert np.abs(ud - want).max() <= 1e-13 * np.abs(want).max()
+    others = [1 + k for k in range(d) if k != axis]
+    assert np.all(ud[others] == 0.0)
+
+
+@pytest.mark.parametrize("d,axis", [(2, 0), (2, 1), (3, 1)])
+def test_burgers_along_one_axis_reproduces_1d(d, axis):
+    L = 6 if d == 2 else 4
+    p1, q1 = I.burgers_1d(L=L, eps=0.0, min_level=2, rk_order=2, time_mode=I.TIME_GTS)
+    p1 = p1.replace(adapt_mode=I.ADAPT_NEVER)
+    dt, n = 0.4 / (1 << L), 10
+    u1 = _run(p1, q1, dt, n)[0]
+    nn = 1 << L
+    shape = [1] * d
+    shape[d - 1 - axis] = nn
+    qd = np.broadcast_to(q1[0].reshape(shape), (nn,) * d)[None].copy()
+    ud = _run(p1.replace(dim=d), qd, dt, n)[0]
+    want = np.broadcast_to(u1.reshape(shape), (nn,) * d)
+    assert np.abs(ud - want).max() <= 1e-14
