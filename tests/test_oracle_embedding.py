@@ -70,3 +70,23 @@ def test_burgers_along_one_axis_reproduces_1d(d, axis):
     ud = _run(p1.replace(dim=d), qd, dt, n)[0]
     want = np.broadcast_to(u1.reshape(shape), (nn,) * d)
     assert np.abs(ud - want).max() <= 1e-14
+
+
+@pytest.mark.parametrize("rk,mode,flux", [(3, I.TIME_LT, 0), (2, I.TIME_LT, 1), (3, I.TIME_GTS, 0)])
+def test_adaptive_2d_solve_is_transpose_invariant(rk, mode, flux):
+    """Swapping x and y in the data (and rho u with rho v) swaps them in the
+    whole adaptive solve: the same tree transposed, the same values to
+    round-off (the x and y flux differences are summed in the other order).
+    This ties together the tensor-product prediction, the detail norm, the
+    grading closure and both flux directions in a genuinely 2D flow."""
+    p, q = I.euler_2d_quadrants(L=6, eps=1e-3, min_level=2, rk_order=rk, time_mode=mode)
+    p = p.replace(flux=flux)
+    qt = q.transpose(0, 2, 1)[[0, 2, 1, 3]].copy()
+    a, b = oracle.Oracle(p, q), oracle.Oracle(p, qt)
+    a.step(0.05)
+    b.step(0.05)
+    ka, kb = a.leaves()[0], b.leaves()[0]
+    assert {tuple(r) for r in ka[:, :3].tolist()} == {(l, j, i) for l, i, j in kb[:, :3].tolist()}
+    assert a.stats()["iters"] == b.stats()["iters"]
+    ua, ub = a.uniform(), b.uniform().transpose(0, 2, 1)[[0, 2, 1, 3]]
+    assert np.abs(ua - ub).max() <= 1e-13 * np.abs(ua).max()
