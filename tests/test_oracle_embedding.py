@@ -90,3 +90,22 @@ def test_adaptive_2d_solve_is_transpose_invariant(rk, mode, flux):
     assert a.stats()["iters"] == b.stats()["iters"]
     ua, ub = a.uniform(), b.uniform().transpose(0, 2, 1)[[0, 2, 1, 3]]
     assert np.abs(ua - ub).max() <= 1e-13 * np.abs(ua).max()
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+def test_adaptive_3d_blast_keeps_the_cube_symmetry(flux):
+    """The 3D blast (a ball at the centre of the unit cube, Neumann walls) is
+    symmetric under every swap of two axes, so the adaptive LT solve must be:
+    the leaf set maps onto itself and the fields onto themselves with the
+    momentum components swapped (z-direction handling included)."""
+    p, q = I.euler_3d_blast(L=5, eps=1e-2, min_level=2, precision=I.PREC_FP64)
+    o = oracle.Oracle(p.replace(flux=flux), q)
+    o.step(0.02)
+    u = o.uniform()  # [v][z][y][x]
+    keys = {tuple(r) for r in o.leaves()[0].tolist()}  # (level, i, j, k) = (level, x, y, z)
+    for axes, comps, swap in (((1, 3, 2), [0, 2, 1, 3, 4], (1, 0, 2)),
+                              ((3, 2, 1), [0, 3, 2, 1, 4], (2, 1, 0)),
+                              ((2, 1, 3), [0, 1, 3, 2, 4], (0, 2, 1))):
+        up = u.transpose((0,) + axes)[comps]
+        assert np.abs(u - up).max() <= 1e-13 * np.abs(u).max()
+        assert {(r[0],) + tuple(r[1 + s] for s in swap) for r in keys} == keys
