@@ -53,7 +53,7 @@ def _args():
     ap.add_argument("--t-end", type=float, default=T_END)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
-                    help="skip the batched-instances and serving measurements")
+                    help="skip the batched-instances, serving and paper-experiment measurements")
     ap.add_argument("--profile-run", action="store_true",
                     help="only the timed LT solves (no e2e / GTS / peaks); for ncu captures")
     ap.add_argument("--level", type=int, default=10, help="finest level (profiling runs)")
