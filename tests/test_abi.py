@@ -219,3 +219,19 @@ def test_ctypes_config_matches_the_c_struct(tmp_path, which):
     declared = [re.sub(r"\[.*?\]", "", n).strip()
                 for decl in re.findall(r"\b(?:int|double)\s+([^;]+);", body) for n in decl.split(",")]
     assert declared == names
+
+
+def test_readme_c_example_compiles_against_the_header(tmp_path):
+    """The C usage example in the README compiles against include/mrlt.h
+    (compiled only: running it needs a GPU)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    txt = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", txt, flags=re.S)
+    assert blocks, "no C example in the README"
+    src = tmp_path / "example.c"
+    src.write_text(blocks[0])
+    subprocess.run(["gcc", "-std=c99", "-D_DEFAULT_SOURCE", "-Wall", "-Werror", "-c", "-I",
+                    os.path.join(ROOT, "include"), "-o", str(tmp_path / "example.o"), str(src)], check=True)
