@@ -207,10 +207,13 @@ mr_status mr_profile(mr_solver* h, int enable);
  * every GPU that loads the library until the process exits.  The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress,
  * with the device current), so make the first call on each device before any
- * stream capture.  Work is only enqueued on cuda_stream: mass_dev is valid once
- * the stream reaches it.  Every call uses the same array, which keeps the
- * previous call's partial sums; calls that overlap on the GPU (other streams
- * or other threads) race on it and must be serialised by the caller. */
+ * stream capture.  The looked-up address is cached per device (safely under
+ * concurrent first calls from several host threads); a cudaDeviceReset
+ * invalidates it, so do not call this after resetting a device in the same
+ * process.  Work is only enqueued on cuda_stream: mass_dev is valid once the
+ * stream reaches it.  Every call uses the same array, which keeps the previous
+ * call's partial sums; calls that overlap on the GPU (other streams or other
+ * threads) race on it and must be serialised by the caller. */
 mr_status mr_leaf_mass_noalloc(int dim, const double* lo, const double* hi, const int* keys_dev,
                                const double* values_dev, long long n_leaves, int m, double* mass_dev,
                                void* cuda_stream, char* msg, size_t msg_cap);

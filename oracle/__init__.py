@@ -98,7 +98,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """One MR/MRLT solve on the host (same calls as the CUDA library)."""
 
-    READ_LEAF_KEYS, READ_LEAF_VALUES, READ_UNIFORM, READ_STATS, READ_FIELDS = 0, 1, 2, 3, 4
+    READ_LEAF_KEYS, READ_LEAF_VALUES, READ_UNIFORM, READ_STATS, READ_FIELDS, READ_NODES = 0, 1, 2, 3, 4, 5
 
     def __init__(self, problem, q0: np.ndarray):
         lib = _load()
@@ -166,6 +166,13 @@ class Oracle:
         """stored per-leaf values [n, 8, m]: q^n, q*, q**, q^{n+1},
         NERK theta=1/2, 1/4, 3/4 and the Eq. 14 extrapolation"""
         return self._read(self.READ_FIELDS, np.float64, (-1, 8, self.m))
+
+    def nodes(self):
+        """internal nodes as stored by the latest iteration: (keys int [n,4] =
+        level,i,j,k ; fields float64 [n,7,m] = q^n, q*, q**, q^{n+1}, half-step
+        value, theta=1/4 and theta=3/4 values)"""
+        rows = self._read(self.READ_NODES, np.float64, (-1, 4 + 7 * self.m))
+        return rows[:, :4].astype(np.int64), rows[:, 4:].reshape(-1, 7, self.m)
 
     def uniform(self) -> np.ndarray:
         n = 1 << self.p.max_level

@@ -9,12 +9,13 @@
  * NERK partial sums, Sec. 3 "Compact formulation").  Readings of passages the
  * paper leaves open are marked READING and are listed in the design notes.
  *
- * Parity unpinned (no test outside this file can fix them):
+ * Parity unpinned (no test outside this file can fix it):
  *  - beta = 1/8 in the AUSM+ Mach splitting (ausm_mach): taken as Liou (1996)
- *    publishes it; the other AUSM+ terms are pinned by the flux tests;
- *  - the internal-child branches of the stage-2/3 projections (Alg. 4, Eq. 15;
- *    Alg. 6): implemented as printed, but on a graded tree with radius-2
- *    stencils no leaf value ever depends on them.
+ *    publishes it; the other AUSM+ terms are pinned by the flux tests.
+ * The internal-child values of the stage-2/3 projections (Eq. 15, Alg. 6) reach
+ * no leaf value on a graded tree with radius-2 stencils; they are read back
+ * through OR_READ_NODES and pinned on a profile whose exact solution is linear
+ * in time (every stored value then equals the exact one at its instant).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so the
  * same source gives the same bits on x86-64 and aarch64).
@@ -570,8 +571,25 @@ static void project_mean(Orc* o, int l, double** src, double** dst)
     }
 }
 
-/* Alg. 4: projection inside the second RK step -- leaf children contribute
- * their Eq. 14 extrapolation, internal children 2 q* - q^n (Eq. 15) */
+/* Value of node (l, id) at t^n + 2 dt_l, extrapolated from its own stage
+ * values: a leaf's Eq. 14 value q* + k2 (stored as QX by its second stage), an
+ * internal node's Eq. 15 value 2 q* - q^n (its q* is the projected value at
+ * t^n + dt_l). */
+static void value_two_steps(Orc* o, int l, long id, double* out)
+{
+    int v;
+    if (o->st[l][id] == 1) {
+        memcpy(out, V(o->QX, l, id), sizeof(double) * o->m);
+        return;
+    }
+    const double* s1 = V(o->Q1, l, id);
+    const double* s0 = V(o->Q0, l, id);
+    for (v = 0; v < o->m; v++) out[v] = 2.0 * s1[v] - s0[v];
+}
+
+/* q* of the internal nodes of level l for the second stage of their level:
+ * their value at t^n + dt_l = t^n + 2 dt_{l+1}, the mean (Eq. 3) of the
+ * children's values at that instant (Eqs. 14-15); this is Alg. 4. */
 static void project_rk2(Orc* o, int l)
 {
     int m = o->m, v, t, c[3], nch = nchild(o);
@@ -579,46 +597,32 @@ static void project_rk2(Orc* o, int l)
     for (id = 0; id < o->nc[l]; id++) {
         if (o->st[l][id] != 2) continue;
         coords(o, l, id, c);
-        double acc[MMAX] = {0};
+        double acc[MMAX] = {0}, w[MMAX];
         for (t = 0; t < nch; t++) {
-            long ch = child_id(o, l, c, t);
-            if (o->st[l + 1][ch] == 1) {
-                const double* s = V(o->QX, l + 1, ch);
-                for (v = 0; v < m; v++) acc[v] += s[v];
-            } else {
-                const double* s1 = V(o->Q1, l + 1, ch);
-                const double* s0 = V(o->Q0, l + 1, ch);
-                for (v = 0; v < m; v++) acc[v] += 2.0 * s1[v] - s0[v];
-            }
+            value_two_steps(o, l + 1, child_id(o, l, c, t), w);
+            for (v = 0; v < m; v++) acc[v] += w[v];
         }
         double* D = V(o->Q1, l, id);
         for (v = 0; v < m; v++) D[v] = acc[v] / nch;
     }
 }
 
-/* Alg. 6: projection inside the third RK step -- children's values at
- * t^n + dt_{l+1} become q** of the node; its own value at t^n + dt_l follows
- * from Eq. 16 (READING: with the theta values implied by the projected q**,
- * Eq. 16 reduces to 2 q** - q^n). */
+/* Stage-3 values of the internal nodes of level l (Alg. 6): q** is their
+ * value at t^n + dt_{l+1}, the mean (Eq. 3) of the children's end values
+ * (every child, leaf or internal, ends its first sub-step there), and the end
+ * value at t^n + dt_l follows from Eq. 16 (READING: with the theta values
+ * implied by the projected q**, Eq. 16 reduces to 2 q** - q^n). */
 static void project_rk3(Orc* o, int l)
 {
-    int m = o->m, v, t, c[3], nch = nchild(o);
+    int m = o->m, v;
     long id;
+    project_mean(o, l, o->QE, o->Q2);
     for (id = 0; id < o->nc[l]; id++) {
         if (o->st[l][id] != 2) continue;
-        coords(o, l, id, c);
-        double acc[MMAX] = {0};
-        for (t = 0; t < nch; t++) {
-            const double* s = V(o->QE, l + 1, child_id(o, l, c, t));
-            for (v = 0; v < m; v++) acc[v] += s[v];
-        }
-        double* q2 = V(o->Q2, l, id);
-        double* qe = V(o->QE, l, id);
+        const double* q2 = V(o->Q2, l, id);
         const double* q0 = V(o->Q0, l, id);
-        for (v = 0; v < m; v++) {
-            q2[v] = acc[v] / nch;
-            qe[v] = 2.0 * q2[v] - q0[v];
-        }
+        double* qe = V(o->QE, l, id);
+        for (v = 0; v < m; v++) qe[v] = 2.0 * q2[v] - q0[v];
     }
 }
 
@@ -1415,11 +1419,32 @@ int or_read(void* h, int what, void* buf, size_t cap, size_t* used)
     else if (what == OR_READ_UNIFORM) need = (size_t)o->nc[o->L] * o->m * sizeof(double);
     else if (what == OR_READ_STATS) need = 64 * sizeof(double);
     else if (what == OR_READ_FIELDS) need = (size_t)nleaf * 8 * o->m * sizeof(double);
-    else return OR_E_INVALID;
+    else if (what == OR_READ_NODES) {
+        long ninner = 0;
+        for (l = o->lb; l <= o->L; l++)
+            for (id = 0; id < o->nc[l]; id++) ninner += o->st[l][id] == 2;
+        need = (size_t)ninner * (4 + 7 * o->m) * sizeof(double);
+    } else return OR_E_INVALID;
     if (used) *used = need;
     if (!buf) return OR_OK;
     if (cap < need) return OR_E_INVALID;
-    if (what == OR_READ_FIELDS) { /* per leaf: Q0 Q1 Q2 QE NH N1 N3 QX */
+    if (what == OR_READ_NODES) { /* per internal node: l i j k, Q0 Q1 Q2 QE XH N1 N3 */
+        long i = 0;
+        int m = o->m, f;
+        for (l = o->lb; l <= o->L; l++)
+            for (id = 0; id < o->nc[l]; id++) {
+                if (o->st[l][id] != 2) continue;
+                double* row = (double*)buf + i * (4 + 7 * m);
+                double** F[7] = {o->Q0, o->Q1, o->Q2, o->QE, o->XH, o->N1, o->N3};
+                coords(o, l, id, c);
+                row[0] = l;
+                row[1] = c[0];
+                row[2] = c[1];
+                row[3] = c[2];
+                for (f = 0; f < 7; f++) memcpy(row + 4 + f * m, V(F[f], l, id), sizeof(double) * m);
+                i++;
+            }
+    } else if (what == OR_READ_FIELDS) { /* per leaf: Q0 Q1 Q2 QE NH N1 N3 QX */
         long i = 0;
         int m = o->m, f;
         for (l = o->lb; l <= o->L; l++)

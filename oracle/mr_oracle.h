@@ -49,8 +49,12 @@ enum {
     OR_READ_LEAF_VALUES = 1, /* double [n_leaves][m] (level-major, then cell)  */
     OR_READ_UNIFORM = 2,     /* double [m][2^{dL}]: inverse MR transform to L  */
     OR_READ_STATS = 3,       /* double [64], see or_stats layout in the .c     */
-    OR_READ_FIELDS = 4       /* double [n_leaves][8][m]: q^n q* q** q^{n+1}
+    OR_READ_FIELDS = 4,      /* double [n_leaves][8][m]: q^n q* q** q^{n+1}
                                 NERK(1/2) NERK(1/4) NERK(3/4) Eq.14 value      */
+    OR_READ_NODES = 5        /* double [n_internal][4 + 7 m]: level, i, j, k, then
+                                q^n, q*, q**, q^{n+1}, half-step value (Eq. 17),
+                                theta=1/4 (Alg. 9), theta=3/4 (Eq. 20) as stored
+                                by the latest iteration                        */
 };
 
 int  or_create(const or_config* cfg, const double* q0_finest, void** out);

@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -28,7 +29,10 @@ constexpr int kMaxDevices = 64;
 // reads, so nothing needs clearing, but concurrent calls share this array
 static __device__ __align__(256) double g_noalloc_partial[kBlocks * kMaxVars];
 
-double* g_partial_addr[kMaxDevices] = {};
+// device address of g_noalloc_partial per device, looked up on the first call
+// on that device; atomic, so that host threads making their first calls at
+// the same time never race on the cache (they store the same value)
+std::atomic<double*> g_partial_addr[kMaxDevices] = {};
 
 void put_msg(char* msg, size_t cap, const char* text)
 {
@@ -99,7 +103,8 @@ extern "C" mr_status mr_leaf_mass_noalloc(int dim, const double* lo, const doubl
         return MR_E_CUDA;
     }
     // once per device, with that device current: device address of the scratch
-    if (!g_partial_addr[dev]) {
+    double* partial = g_partial_addr[dev].load(std::memory_order_acquire);
+    if (!partial) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
         if (e != cudaSuccess || !p) {
@@ -107,13 +112,14 @@ extern "C" mr_status mr_leaf_mass_noalloc(int dim, const double* lo, const doubl
             put_msg(msg, msg_cap, buf);
             return MR_E_CUDA;
         }
-        g_partial_addr[dev] = (double*)p;
+        partial = (double*)p;
+        g_partial_addr[dev].store(partial, std::memory_order_release);
     }
     double vol0 = 1.0;
     for (int k = 0; k < dim; ++k) vol0 *= hi[k] - lo[k];
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    k_mass_partial<<<kBlocks, kThreads, 0, st>>>(keys_dev, values_dev, n_leaves, m, vol0, dim, g_partial_addr[dev]);
-    k_mass_final<<<1, 32, 0, st>>>(g_partial_addr[dev], m, mass_dev);
+    k_mass_partial<<<kBlocks, kThreads, 0, st>>>(keys_dev, values_dev, n_leaves, m, vol0, dim, partial);
+    k_mass_final<<<1, 32, 0, st>>>(partial, m, mass_dev);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(buf, sizeof buf, "mr_leaf_mass_noalloc: launch failed: %s", cudaGetErrorString(e));

@@ -1,13 +1,19 @@
 """Request server (C-ABI `mr_server`): problems submitted over time, admitted
 at round boundaries under a device-memory budget, finished at their own end
 times.  Each result must equal the same problem solved alone, bit for bit
-(the server runs the same kernels in the same order per problem)."""
+(the server runs the same kernels in the same order per problem), and the
+FP64 oracle: leaf by leaf within 1e-12 in FP64, and within the mixed-precision
+L1 bound (derived in test_gpu_mixed) in the mixed mode."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1905_08717_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
+TOL = 1e-12
+U32 = 2.0 ** -24
+C_FLUX = 64
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -45,12 +51,36 @@ def _drain(srv, done, seconds=300.0):
     raise AssertionError("server did not drain")
 
 
-@pytest.mark.parametrize("caps", [(0, 0), (5, 152)])
-def test_serve_results_equal_standalone(caps):
+def _vs_oracle(r, p, q, t):
+    """a served result against the FP64 oracle run of the same request"""
+    ref = oracle.Oracle(p.replace(precision=I.PREC_FP64), q)
+    ref.step(t)
+    if p.precision == I.PREC_FP64:
+        kr, vr = r.leaves()
+        ko, vo = ref.leaves()
+        assert np.array_equal(kr, ko), (p.name, len(kr), len(ko))
+        err = np.abs(vr - vo) / (np.abs(vo) + np.abs(vo).max(axis=0) + 1e-300)
+        assert err.max() <= TOL, (p.name, err.max())
+    else:
+        n = ref.stats()["iters"]
+        tol = n * 6 * C_FLUX * U32 * p.cfl + p.eps * 1e-2
+        a, b = r.uniform(), ref.uniform()
+        a = a.reshape(a.shape[0], -1)
+        b = b.reshape(b.shape[0], -1)
+        e = np.abs(a - b).sum(axis=1) / np.maximum(np.abs(b).sum(axis=1), 1e-300)
+        assert e.max() <= tol, (p.name, e, tol)
+    ref.close()
+
+
+@pytest.mark.parametrize("caps,prec", [((0, 0), I.PREC_FP64), ((5, 152), I.PREC_FP64),
+                                       ((0, 0), I.PREC_MIXED)])
+def test_serve_results_equal_standalone(caps, prec):
     """caps: stage-launch block caps for the first and the later requests
-    (0: the default launch shape); the results must not depend on them"""
+    (0: the default launch shape); the results must not depend on them.
+    Every served result also matches the FP64 oracle (see the module note)."""
     import paper_1905_08717_gb300 as pkg
     probs, qs, ends = _requests()
+    probs = [p.replace(precision=prec) for p in probs]
     srv = pkg.Server(mem_budget_bytes=8 << 30, max_active=16)
     srv.set_grid_cap(caps[0])
     ids, done = [], []
@@ -73,6 +103,7 @@ def test_serve_results_equal_standalone(caps):
         ks, vs = s.leaves()
         assert np.array_equal(kr, ks) and np.array_equal(vr, vs), p.name
         assert r.stats()["t"] == t
+        _vs_oracle(r, p, q, t)
         s.close()
         srv.release(rid)
     assert srv.memory() == 0

@@ -215,8 +215,9 @@ COLUMNS = {"FV/RK2": (1, 2, 0, False), "MR/RK2": (2, 2, 0, True), "MRLT/NERK2": 
 
 def _check_orders(got, col, name, gold):
     if name == "MRLT/NERK3":
-        # paper: drops from 3 towards 2 (1.79, 1.92); our readings approach 2 from above
-        assert all(1.6 < g < 2.9 for g in got), got
+        # paper: 1.79, 1.92 at these steps, tending to 2; the oracle tends to 2
+        # from above (its asymptote is pinned by test_nerk3_lt_asymptotic_order)
+        assert all(1.9 < g < 2.9 for g in got), got
         assert got[1] < got[0]
     else:
         tol = 0.05
@@ -230,6 +231,67 @@ def test_time_order_table_reduced(name):
     col, rk, mode, two = COLUMNS[name]
     got = _orders(7, [6.25e-4, 3.125e-4, 1.5625e-4, 7.8125e-5], rk, mode, two)
     _check_orders(got, col, name, _golden())
+
+
+def test_nerk3_lt_asymptotic_order():
+    """Sec. 4.5: MRLT/NERK3 loses third order on the two-level grid; its time
+    order tends to 2 as dt -> 0 (Table 1: 1.79, 1.92).  On the reduced grid,
+    continued to dt = 1.95e-5, the observed order decreases at every halving
+    and ends within 2 +- 0.1: a scheme that kept order 3 (no LT perturbation)
+    or fell to first order (a first-order coarse half-step value, as in the
+    classic MRLT/RK2 column) fails.  NERK2 on the same steps stays at 2."""
+    dts = [6.25e-4, 3.125e-4, 1.5625e-4, 7.8125e-5, 3.90625e-5, 1.953125e-5]
+    got = _orders(7, dts, 3, 1, True)
+    assert all(b < a for a, b in zip(got, got[1:])), got
+    assert abs(got[-1] - 2.0) < 0.1, got
+    got2 = _orders(7, dts[-3:], 2, 1, True)
+    assert abs(got2[-1] - 2.0) < 0.01, got2
+
+
+def _linear_profile_run(rk):
+    """Linear advection q_t + q_x = 0 of q0 = x + 2 (cell averages = centre
+    values) on a fixed four-level nested tree, one LT iteration at n = 0 (every
+    level active).  Returns the internal nodes away from the periodic wrap."""
+    L, lb = 7, 3
+    lev = np.full(1 << L, L - 3, np.uint8)
+    lev[40:88] = L - 2
+    lev[48:80] = L - 1
+    lev[56:72] = L
+    x = (np.arange(1 << L) + 0.5) / (1 << L)
+    p = I.Problem(dim=1, equation=I.EQ_ADVECTION, max_level=L, min_level=lb, eps=0.0, rk_order=rk,
+                  adapt_mode=I.ADAPT_NEVER, phys=(1.0,) + (0.0,) * 7)
+    o = oracle.Oracle(p, (x + 2.0)[None, :])
+    o.set_tree(lev)
+    dt = 0.25 / (1 << L)
+    o.iterate(dt, 1)
+    keys, f = o.nodes()
+    xc = (keys[:, 1] + 0.5) / 2.0 ** keys[:, 0]
+    dtl = dt * 2.0 ** (L - keys[:, 0])
+    keep = (xc > 0.25) & (xc < 0.75)
+    return keys[keep], f[keep, :, 0], xc[keep], dtl[keep]
+
+
+@pytest.mark.parametrize("rk", [2, 3])
+def test_internal_nodes_exact_for_linear_in_time_solution(rk):
+    """The exact solution q = (x - t) + 2 is linear in space and time: the
+    centred flux and the prediction (Eq. 4) are exact on it, the right-hand
+    side is constant, so every RK stage, NERK value (Sec. 3) and tree refresh
+    (Eqs. 14-18, 20-21) must reproduce the exact value at its own instant.
+    This observes the internal-node values no leaf reads on a graded tree,
+    including the internal-child branches of Alg. 4 (Eq. 15) and Alg. 6:
+    q* = q(t^n + dt_l) after the stage-2 projection, half-step value (Eq. 17)
+    = q(t^n + dt_l/2); RK3 also q** = q(t^n + dt_l/2), end value q(t^n + dt_l),
+    theta = 1/4 and 3/4 values q(t^n + dt_l/4), q(t^n + 3 dt_l/4)."""
+    keys, f, xc, dtl = _linear_profile_run(rk)
+    # nodes with an internal child exist on three levels of the check region
+    assert len(set(keys[:, 0])) >= 3 and len(keys) >= 12
+    ex = lambda th: xc - th * dtl + 2.0
+    want = {0: ex(0.0), 1: ex(1.0), 4: ex(0.5)}
+    if rk == 3:
+        want.update({2: ex(0.5), 3: ex(1.0), 5: ex(0.25), 6: ex(0.75)})
+    for col, w in want.items():
+        err = np.abs(f[:, col] - w).max()
+        assert err < 1e-13, (col, err)
 
 
 @pytest.mark.slow

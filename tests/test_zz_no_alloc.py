@@ -2,7 +2,8 @@
 device memory (their GPU memory is held by another allocator, or they run in
 a loop that must not pay for cudaMalloc).  It must give the same per-variable
 totals as MR_READ_STATS, call after call, although its only scratch is a fixed
-array inside the library that every call reuses.  Collected last on purpose."""
+array inside the library that every call reuses, and it must leave the
+device's free memory untouched.  Collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -22,17 +23,22 @@ def torch():
     return t
 
 
-def _check(torch, pkg, p, solver, out):
+def _state(torch, p, solver):
+    """leaf keys and values on the device, the STATS totals, and their scale"""
     keys, vals = solver.leaves()
     want = solver.stats()["mass"]
-    kd = torch.from_numpy(np.ascontiguousarray(keys)).cuda()
-    vd = torch.from_numpy(np.ascontiguousarray(vals)).cuda()
-    pkg.leaf_mass_noalloc(p.dim, p.lo, p.hi, kd.data_ptr(), vd.data_ptr(), len(keys), p.nvars(),
-                          out.data_ptr())
-    torch.cuda.synchronize()
-    got = out.cpu().numpy()
     vol = np.prod([(p.hi[k] - p.lo[k]) for k in range(p.dim)]) * 2.0 ** (-p.dim * keys[:, 0])
     scale = (np.abs(vals) * vol[:, None]).sum(axis=0)
+    kd = torch.from_numpy(np.ascontiguousarray(keys)).cuda()
+    vd = torch.from_numpy(np.ascontiguousarray(vals)).cuda()
+    return kd, vd, len(keys), want, scale
+
+
+def _call(torch, pkg, p, st, out):
+    kd, vd, n, want, scale = st
+    pkg.leaf_mass_noalloc(p.dim, p.lo, p.hi, kd.data_ptr(), vd.data_ptr(), n, p.nvars(), out.data_ptr())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
     assert np.all(np.abs(got - want) <= TOL * scale), (got, want)
     return got
 
@@ -48,14 +54,25 @@ def test_leaf_mass_noalloc_matches_stats_on_consecutive_calls(torch, case):
         q = q + 0.5
         times = (0.1, 0.3)
     solver = pkg.Solver(p, q)
-    out = torch.full((p.nvars(),), float("nan"), dtype=torch.float64, device="cuda")
-    first = None
-    for t in times:  # two calls in a row on different states share the scratch
+    states = []
+    for t in times:
         solver.step(t)
-        got = _check(torch, pkg, p, solver, out)
-        if first is None:
-            first = got
-    assert not np.array_equal(first, got) or case == "burgers1d"
+        states.append(_state(torch, p, solver))
+    out = torch.full((p.nvars(),), float("nan"), dtype=torch.float64, device="cuda")
+    _call(torch, pkg, p, states[0], out)  # first call on the device: address look-up
+    free0, res0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    # two calls in a row on different states share the scratch, then the first again
+    got = [_call(torch, pkg, p, st, out) for st in (states[0], states[1], states[0])]
+    assert torch.cuda.mem_get_info()[0] == free0, "device free memory changed"
+    assert torch.cuda.memory_reserved() == res0
+    assert np.array_equal(got[0], got[2])
+    if case == "euler2d":
+        assert not np.array_equal(got[0], got[1])
+    else:  # periodic Burgers with flux registers conserves the initial total exactly
+        m0 = q.sum() / q.size
+        for g in got:
+            assert abs(g[0] - m0) <= TOL * np.abs(q).sum() / q.size, (g, m0)
+    solver.close()
 
 
 def test_leaf_mass_noalloc_rejects_sizes_beyond_its_scratch(torch):
