@@ -40,7 +40,7 @@ typedef enum {
     MR_E_INVALID = 1, /* bad argument or configuration                    */
     MR_E_NOMEM = 2,   /* device or host allocation failed                 */
     MR_E_CUDA = 3,    /* a CUDA runtime call failed                       */
-    MR_E_TIMEOUT = 4, /* reserved: a bounded device wait gave up          */
+    MR_E_TIMEOUT = 4, /* a bounded device wait (grid barrier) gave up      */
     MR_E_STATE = 5,   /* call not valid in the current state, or the tree
                          invariant was found broken on the device          */
     MR_E_NUMERIC = 6  /* a non-finite value appeared in the solution       */
@@ -157,6 +157,32 @@ mr_status mr_sync(mr_solver* h);
  * for a NULL handle or ctas < 0; MR_E_CUDA if that wait fails.  The paper has
  * no counterpart: it runs one problem on one CPU core. */
 mr_status mr_set_grid_cap(mr_solver* h, int ctas);
+
+/* How fine iterations are launched.  MR_LAUNCH_GRAPH (the default) launches
+ * one kernel per phase of an iteration (projections, refreshes and stage
+ * sweeps per level, the adaptation passes, compaction, reflux; Algs. 3-9),
+ * whole macro steps replayed as a CUDA graph; batch instances and served
+ * requests always use it, because they run concurrently on their own streams.
+ * MR_LAUNCH_PERSISTENT runs the iterations of a macro step in one cooperative
+ * launch of a persistent kernel whose CTAs all stay resident, the phases
+ * separated by grid-wide barriers instead of kernel boundaries: two launches
+ * per macro step instead of thousands.  Both modes run the same device code in
+ * the same order; the compiler may contract a different set of multiply-adds
+ * in the two kernels, so they agree to FP64 round-off rather than bit for bit.
+ * A barrier wait is bounded (4 s): if it gives up, the call returns
+ * MR_E_TIMEOUT and the solver should be destroyed.  Only at a macro-step
+ * boundary (MR_E_STATE otherwise).  The paper has no counterpart. */
+enum { MR_LAUNCH_PERSISTENT = 0, MR_LAUNCH_GRAPH = 1 };
+mr_status mr_set_launch_mode(mr_solver* h, int mode);
+
+/* Self-test of the bounded grid barrier used by MR_LAUNCH_PERSISTENT:
+ * launches `ctas` (1..1024) small CTAs that meet at one barrier which expects
+ * `missing` more CTAs than exist.  With missing = 0 the barrier completes and
+ * the call returns MR_OK; with missing > 0 nobody releases it, every CTA gives
+ * up after limit_s seconds (0 < limit_s <= 60), and the call returns
+ * MR_E_TIMEOUT with the device still usable.  Allocates and frees 16 bytes of
+ * device memory; synchronises cuda_stream.  The paper has no counterpart. */
+mr_status mr_selftest_grid_wait(int ctas, int missing, double limit_s, void* cuda_stream);
 
 /* What mr_read returns. */
 enum {

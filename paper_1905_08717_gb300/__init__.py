@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "csrc", "libmrlt.so")
 
 MR_READ_LEAF_KEYS, MR_READ_LEAF_VALUES, MR_READ_UNIFORM, MR_READ_STATS, MR_READ_PROFILE = 0, 1, 2, 3, 4
+MR_LAUNCH_PERSISTENT, MR_LAUNCH_GRAPH = 0, 1
 STATUS = {0: "MR_OK", 1: "MR_E_INVALID", 2: "MR_E_NOMEM", 3: "MR_E_CUDA",
           4: "MR_E_TIMEOUT", 5: "MR_E_STATE", 6: "MR_E_NUMERIC"}
 
@@ -70,6 +71,8 @@ def library() -> ctypes.CDLL:
         lib.mr_set_async.argtypes = [vp, ctypes.c_int]
         lib.mr_sync.argtypes = [vp]
         lib.mr_set_grid_cap.argtypes = [vp, ctypes.c_int]
+        lib.mr_set_launch_mode.argtypes = [vp, ctypes.c_int]
+        lib.mr_selftest_grid_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]
         lib.mr_batch_set_grid_cap.argtypes = [vp, ctypes.c_int]
         lib.mr_server_set_grid_cap.argtypes = [vp, ctypes.c_int]
         lib.mr_release_cached_memory.argtypes = []
@@ -105,7 +108,8 @@ def library() -> ctypes.CDLL:
         lib.mr_server_destroy.argtypes = [vp]
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
                      "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create", "mr_create_from_state",
-                     "mr_batch_step", "mr_set_async", "mr_sync", "mr_set_grid_cap", "mr_batch_set_grid_cap", "mr_server_set_grid_cap",
+                     "mr_batch_step", "mr_set_async", "mr_sync", "mr_set_grid_cap", "mr_set_launch_mode",
+                     "mr_selftest_grid_wait", "mr_batch_set_grid_cap", "mr_server_set_grid_cap",
                      "mr_server_create", "mr_server_submit", "mr_server_advance",
                      "mr_server_poll", "mr_server_status", "mr_server_release"):
             getattr(lib, name).restype = ctypes.c_int
@@ -149,6 +153,13 @@ def leaf_mass_noalloc(dim: int, lo, hi, keys_ptr: int, values_ptr: int, n_leaves
                                  ctypes.c_void_p(_stream_handle(stream)), msg, len(msg))
     if r != 0:
         raise MRError(r, msg.value.decode())
+
+
+def selftest_grid_wait(ctas: int, missing: int, limit_s: float, stream=None) -> int:
+    """Binding of mr_selftest_grid_wait: the status (0 = MR_OK, 4 = MR_E_TIMEOUT)
+    of one bounded grid barrier that `missing` CTAs never reach."""
+    return library().mr_selftest_grid_wait(int(ctas), int(missing), float(limit_s),
+                                           ctypes.c_void_p(_stream_handle(stream)))
 
 
 def release_cached_memory() -> None:
@@ -264,6 +275,12 @@ class Solver:
         """at most `ctas` thread blocks per stage-kernel launch (0: fill the
         GPU); the results do not depend on it"""
         self._check(library().mr_set_grid_cap(self._h, int(ctas)), "set_grid_cap")
+
+    def set_launch_mode(self, mode: int):
+        """MR_LAUNCH_PERSISTENT (one cooperative macro-step kernel, the
+        default) or MR_LAUNCH_GRAPH (one kernel per phase); bitwise the same
+        results"""
+        self._check(library().mr_set_launch_mode(self._h, int(mode)), "set_launch_mode")
 
     def _read(self, what, dtype, shape=None, out=None):
         lib = library()

@@ -2,6 +2,7 @@
 // layout, the LT iteration schedule (Alg. 3), the global-step MR iteration,
 // macro steps with the CFL rule, and read-back.
 #include "mrlt.h"
+#include "mrlt_macro.cuh"
 #include "mrlt_tree.cuh"
 
 #include <cmath>
@@ -58,6 +59,15 @@ struct mr_solver {
     // (the footprint of a configuration is projected without creating it)
     size_t bytes = 0;
     bool dry = false;
+    // launch mode: MR_LAUNCH_GRAPH (the default) launches one kernel per phase,
+    // macro steps replayed as CUDA graphs; MR_LAUNCH_PERSISTENT runs the fine
+    // iterations in one cooperative macro-step kernel (mrlt_macro.cuh)
+    int launch_mode = MR_LAUNCH_GRAPH;
+    unsigned* d_bar = nullptr;                 // grid barrier of the macro-step kernel
+    bool wmax_valid = false;                   // g.wmax holds the CFL speed of the current state
+    unsigned long long* d_stamps = nullptr;    // profiling stamps of the macro-step kernel
+    int* d_nstamps = nullptr;
+    double grid_wait_s = 4.0;                  // longest grid-barrier wait
 };
 
 namespace {
@@ -232,8 +242,10 @@ mr_status sync_check(mr_solver* h)
     MR_CK(cudaStreamSynchronize(h->stream));
     if (e) {
         char buf[128];
-        snprintf(buf, sizeof buf, "device reported error bits 0x%x", e);
+        snprintf(buf, sizeof buf, "device reported error bits 0x%x%s", e,
+                 (e & ERR_TIMEOUT) ? " (a grid barrier wait gave up)" : "");
         h->err = buf;
+        if (e & ERR_TIMEOUT) return MR_E_TIMEOUT;
         return (e & ERR_NONFINITE) ? MR_E_NUMERIC : MR_E_STATE;
     }
     return MR_OK;
@@ -359,6 +371,66 @@ bool capture_macro(mr_solver* h, long long nit)
 // iterations per macro step (larger schedules launch directly).
 constexpr long long kMaxGraphIters = 1024;
 
+// Profiling capacity of the macro-step kernel's phase stamps; a profiled run
+// launches at most kProfIters fine iterations per macro-step kernel.
+constexpr int kStampCap = 1 << 15;
+constexpr long long kProfIters = 256;
+
+// Sum the stage phases recorded by the last profiled macro-step kernel:
+// the duration of a phase is the time from its start to the next phase's.
+mr_status drain_stamps(mr_solver* h)
+{
+    int n = 0;
+    MR_CK(cudaMemcpyAsync(&n, h->d_nstamps, sizeof n, cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaStreamSynchronize(h->stream));
+    if (n > kStampCap) n = kStampCap;
+    std::vector<unsigned long long> st((size_t)2 * n);
+    if (n) MR_CK(cudaMemcpyAsync(st.data(), h->d_stamps, st.size() * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i + 1 < n; ++i) {
+        const int kind = (int)(st[2 * i] >> 8), level = (int)(st[2 * i] & 255);
+        if (kind < PH_STAGE1 || kind > PH_STAGE3) continue;
+        const double ms = (double)(st[2 * i + 3] - st[2 * i + 1]) * 1e-6;
+        h->prof_ms += ms;
+        if (level <= LMAX) h->prof_level_ms[level] += ms;
+        ++h->prof_launches;
+    }
+    return MR_OK;
+}
+
+// Iterations [pos, pos + count) of the current macro step in one launch of
+// the persistent macro-step kernel (count <= nit - pos).
+mr_status run_persistent(mr_solver* h, long long count, long long nit)
+{
+    MacroArgs a = {};
+    a.n0 = h->pos;
+    a.n1 = h->pos + count;
+    a.nit = nit;
+    a.adapt_mode = h->cfg.adapt_mode;
+    a.reg = h->reg && !h->K.g.gts;
+    a.end_of_macro = a.n1 == nit;
+    a.bar = h->d_bar;
+    a.limit_ns = (unsigned long long)(h->grid_wait_s * 1e9);
+    a.bc = h->K.bc;
+    if (h->prof) {
+        a.stamps = h->d_stamps;
+        a.nstamps = h->d_nstamps;
+        a.stamp_cap = kStampCap;
+        MR_CK(cudaMemsetAsync(h->d_nstamps, 0, sizeof(int), h->stream));
+    }
+    MR_CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
+    if (launch_macro(h->K.g, h->stream, &a) < 0) {
+        cudaGetLastError();
+        h->err = "macro-step kernel could not be launched (cooperative launch or occupancy query failed)";
+        return MR_E_CUDA;
+    }
+    ++h->K.n;
+    h->wmax_valid = false;
+    if (h->prof) MR_TRY(drain_stamps(h));
+    return MR_OK;
+}
+
 mr_status run_iters(mr_solver* h, double dt, long long n)
 {
     const long long nit = 1LL << (h->K.g.L - h->K.g.lb);
@@ -370,6 +442,27 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
     long long i = 0;
     while (i < n) {
         if (h->pos == 0) h->K.set_dt(dt);
+        if (h->launch_mode == MR_LAUNCH_PERSISTENT) {
+            long long chunk = n - i < nit - h->pos ? n - i : nit - h->pos;
+            if (h->prof && chunk > kProfIters) chunk = kProfIters;
+            MR_TRY(run_persistent(h, chunk, nit));
+            h->iters += chunk;
+            h->pos += chunk;
+            i += chunk;
+            if (h->pos == nit) {
+                h->pos = 0;
+                ++h->macros;
+                h->wmax_valid = true; // the kernel ended with the CFL reduction
+                if (h->async_err) {
+                    MR_CK(cudaMemcpyAsync(h->async_err, h->K.g.err, sizeof(int), cudaMemcpyDeviceToHost,
+                                          h->stream));
+                } else {
+                    MR_TRY(sync_check(h));
+                }
+            }
+            continue;
+        }
+        h->wmax_valid = false;
         bool graph = h->pos == 0 && n - i >= nit && !h->prof && !h->graph_off && nit <= kMaxGraphIters;
         if (graph && !h->macro_exec && !capture_macro(h, nit)) {
             h->graph_off = true; // launch directly from now on
@@ -406,6 +499,10 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
 mr_status cfl_enqueue(mr_solver* h, unsigned long long* bits)
 {
     Grid& g = h->K.g;
+    if (h->wmax_valid) { // computed at the end of the macro-step kernel that led to this state
+        MR_CK(cudaMemcpyAsync(bits, g.wmax, sizeof *bits, cudaMemcpyDeviceToHost, h->stream));
+        return MR_OK;
+    }
     MR_CK(cudaMemsetAsync(g.wmax, 0, sizeof(unsigned long long), h->stream));
     for (int l = g.lb; l <= g.L; ++l) {
         launch_wave(g, h->stream, l);
@@ -466,6 +563,7 @@ mr_status init_state(mr_solver* h, const double* q0)
     h->K.leaf_copy(g.lb, g.L, F_Q0, F_QE);
     h->t = h->dt = 0.0;
     h->iters = h->macros = h->pos = 0;
+    h->wmax_valid = false;
     return sync_check(h);
 }
 
@@ -544,6 +642,7 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     A(dev_alloc(h, &g.wmax, 1));
     A(dev_alloc(h, &g.updates, 1));
     A(dev_alloc(h, &g.work, (LMAX + 1) * 4));
+    A(dev_alloc(h, &h->d_bar, 2));
     if (r == MR_OK && !h->dry &&
         cudaMemsetAsync(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long), h->stream) != cudaSuccess)
         r = MR_E_CUDA; // cumulative counters: never cleared by mr_reset
@@ -604,6 +703,7 @@ mr_status mr_set_tree(mr_solver* h, const unsigned char* lev)
 {
     if (!h || !lev) return MR_E_INVALID;
     if (h->pos != 0) return MR_E_STATE;
+    h->wmax_valid = false;
     Grid& g = h->K.g;
     const int L = g.L, lb = g.lb, d = g.d;
     std::vector<std::vector<uint8_t>> R(L + 1);
@@ -756,6 +856,7 @@ mr_status mr_adapt(mr_solver* h)
 {
     if (!h) return MR_E_INVALID;
     if (h->pos != 0) return MR_E_STATE;
+    h->wmax_valid = false;
     Grid& g = h->K.g;
     h->K.leaf_copy(g.lb, g.L, F_QE, F_Q0);
     for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
@@ -835,6 +936,38 @@ mr_status mr_set_grid_cap(mr_solver* h, int ctas)
     }
     h->K.g.gcap = ctas;
     return MR_OK;
+}
+
+mr_status mr_set_launch_mode(mr_solver* h, int mode)
+{
+    if (!h || (mode != MR_LAUNCH_PERSISTENT && mode != MR_LAUNCH_GRAPH)) return MR_E_INVALID;
+    if (h->pos != 0) return MR_E_STATE;
+    h->launch_mode = mode;
+    return MR_OK;
+}
+
+mr_status mr_selftest_grid_wait(int ctas, int missing, double limit_s, void* cuda_stream)
+{
+    if (ctas < 1 || ctas > 1024 || missing < 0 || !(limit_s > 0.0) || limit_s > 60.0) return MR_E_INVALID;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    unsigned* bar = nullptr;
+    if (cudaMalloc((void**)&bar, 4 * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return MR_E_NOMEM;
+    }
+    int* err = (int*)(bar + 2);
+    int e = 0;
+    mr_status r = MR_OK;
+    if (cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st) != cudaSuccess ||
+        launch_grid_wait_test(st, ctas, missing, (unsigned long long)(limit_s * 1e9), bar, err) != 0 ||
+        cudaMemcpyAsync(&e, err, sizeof e, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        r = MR_E_CUDA;
+    else if (e & ERR_TIMEOUT)
+        r = MR_E_TIMEOUT;
+    cudaGetLastError();
+    cudaFree(bar);
+    return r;
 }
 
 mr_status mr_sync(mr_solver* h)
@@ -940,6 +1073,12 @@ mr_status mr_profile(mr_solver* h, int enable)
             h->ev.resize(2 * 4096);
             h->ev_level.assign(4096, 0);
             for (auto& e : h->ev) MR_CK(cudaEventCreate(&e));
+        }
+        if (!h->d_stamps) { // phase stamps of the macro-step kernel (not part of the footprint)
+            const size_t b0 = h->bytes;
+            MR_TRY(dev_alloc(h, &h->d_stamps, (size_t)2 * kStampCap));
+            MR_TRY(dev_alloc(h, &h->d_nstamps, 1));
+            h->bytes = b0;
         }
         MR_CK(cudaStreamSynchronize(h->stream));
         h->ev_used = 0;
@@ -1132,6 +1271,10 @@ mr_status mr_batch_create(int n, const mr_config* cfgs, const double* const* q0s
         const mr_status r = mr_create(&cfgs[i], q0s[i], st, &h);
         if (r != MR_OK) return fail(i, r);
         h->async_err = &b->errs[i];
+        // instances run concurrently on their own streams: one kernel per
+        // phase (captured graphs), since co-residency of several cooperative
+        // grids is not something the instances could rely on
+        h->launch_mode = MR_LAUNCH_GRAPH;
         b->inst.push_back(h);
     }
     *out = b;
@@ -1299,6 +1442,7 @@ mr_status admit(mr_server* s)
             continue;
         }
         q->h->async_err = &s->errs[q->slot];
+        q->h->launch_mode = MR_LAUNCH_GRAPH; // concurrent requests: as batch instances
         if (s->gcap) mr_set_grid_cap(q->h, s->gcap); // nothing captured yet: cannot fail
         s->used += q->bytes;
         q->state = q->h->t < q->t_end ? 1 : 2;

@@ -36,7 +36,7 @@ constexpr int kTileThreads1 = 128, kTileThreads2 = 256, kTileThreads3 = 256;
 enum Field { F_Q0 = 0, F_Q1, F_Q2, F_QE, F_XH, F_NH, F_N1, F_N3, NFIELD };
 enum Kind { K_WALL = 0, K_LEAF = 1, K_FINER = 2, K_COARSER = 3 };
 enum FlagBits { FL_SIG = 1, FL_BIG = 2, FL_DES = 4, FL_ALLOW = 8, FL_REF = 16 };
-enum ErrBits { ERR_INDEX = 1, ERR_SOURCE = 2, ERR_NONFINITE = 4, ERR_REFLUX = 8 };
+enum ErrBits { ERR_INDEX = 1, ERR_SOURCE = 2, ERR_NONFINITE = 4, ERR_REFLUX = 8, ERR_TIMEOUT = 16 };
 
 struct Grid {
     uint8_t* st;
@@ -118,10 +118,7 @@ struct Ctx {
 __device__ __forceinline__ int wrap_or_mirror(const Grid& g, int l, int k, int p, int& neg)
 {
     const int n = g.n[l];
-    if (g.bc[k] == 0) {
-        p %= n;
-        return p < 0 ? p + n : p;
-    }
+    if (g.bc[k] == 0) return p & (n - 1); // periodic wrap (n = 2^l)
     const int odd = g.bc[k] == 2;
 #pragma unroll 1
     for (int it = 0; it < 8 && (p < 0 || p >= n); ++it) {
@@ -136,8 +133,7 @@ __device__ __forceinline__ bool in_box(const Grid& g, int l, int k, int p, int* 
 {
     const int n = g.n[l];
     if (g.bc[k] == 0) {
-        p %= n;
-        *q = p < 0 ? p + n : p;
+        *q = p & (n - 1); // periodic wrap (n = 2^l)
         return true;
     }
     if (p < 0 || p >= n) return false;
@@ -151,12 +147,13 @@ __device__ __forceinline__ long long cell_id(const Grid& g, int l, int x, int y,
     return (long long)x + n * ((long long)y + n * (long long)z);
 }
 
+// coordinates of cell id on level l (n = 2^l cells per direction)
 __device__ __forceinline__ void cell_xyz(const Grid& g, int l, long long id, int c[3])
 {
-    const long long n = g.n[l];
-    c[0] = (int)(id % n);
-    c[1] = g.d > 1 ? (int)((id / n) % n) : 0;
-    c[2] = g.d > 2 ? (int)(id / (n * n)) : 0;
+    const long long mask = (1LL << l) - 1;
+    c[0] = (int)(id & mask);
+    c[1] = g.d > 1 ? (int)((id >> l) & mask) : 0;
+    c[2] = g.d > 2 ? (int)(id >> (2 * l)) : 0;
 }
 
 __device__ __forceinline__ const double* fbase(const Grid& g, int f, int l)
@@ -326,6 +323,54 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
                 const double w = neg ? -w0 : w0; // an odd-mirror ghost enters negated
 #pragma unroll
                 for (int v = 0; v < M; ++v) out[v] += w * val[v];
+            }
+        }
+    }
+}
+
+// Predictions (Eq. 4, tensor product) of all 2^d children on level l + 1 of
+// the node at in-box coordinates c of level l: the 3^d block around c is read
+// once and enters every child with that child's weights.  Each child's sum
+// runs over the block in the order of predict(), so out[k] equals
+// predict(g, x, l + 1, 2 c + k) term by term.
+template <int D, int M>
+__device__ __forceinline__ void predict_children(const Grid& g, const Ctx& x, int l, const int c[3],
+                                                 double (*out)[M])
+{
+    constexpr int NCH = 1 << D;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k)
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[k][v] = 0.0;
+#pragma unroll(D > 2 ? 1 : 3)
+    for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
+        int nz = 0;
+        const int z = D > 2 ? wrap_or_mirror(g, l, 2, c[2] + dz, nz) : 0;
+#pragma unroll(D > 2 ? 1 : 3)
+        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
+            int nyz = nz;
+            const int y = D > 1 ? wrap_or_mirror(g, l, 1, c[1] + dy, nyz) : 0;
+#pragma unroll
+            for (int dxx = -1; dxx <= 1; ++dxx) {
+                int neg = nyz;
+                const int xx = wrap_or_mirror(g, l, 0, c[0] + dxx, neg);
+                const long long id = cell_id(g, l, xx, y, z);
+                const int st = status(g, l, id);
+                if (st == 0) {
+                    atomicOr(g.err, ERR_SOURCE);
+                    continue;
+                }
+                double val[M];
+                expose<M>(g, x, l, id, st, val);
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    const double wz = D > 2 ? pw((k >> 2) & 1, dz) : 1.0;
+                    const double wyz = wz * (D > 1 ? pw((k >> 1) & 1, dy) : 1.0);
+                    const double w0 = wyz * pw(k & 1, dxx);
+                    const double w = neg ? -w0 : w0; // an odd-mirror ghost enters negated
+#pragma unroll
+                    for (int v = 0; v < M; ++v) out[k][v] += w * val[v];
+                }
             }
         }
     }
@@ -547,4 +592,11 @@ struct Launch; // fwd
 // (-1 when the kernel could not be set up).  lo > hi only sets the kernel up.
 int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg);
 void launch_wave(const Grid& g, cudaStream_t st, int l);
+// one persistent macro-step kernel launch (mrlt_macro.cuh); a == nullptr sets
+// the kernel up only.  Returns 1 when launched, 0 after set-up, -1 on failure.
+struct MacroArgs;
+int launch_macro(const Grid& g, cudaStream_t st, const MacroArgs* a);
+// the bounded grid barrier with `missing` CTAs that never arrive (self-test)
+int launch_grid_wait_test(cudaStream_t st, int ctas, int missing, unsigned long long limit_ns, unsigned* bar,
+                          int* err);
 } // namespace mrlt

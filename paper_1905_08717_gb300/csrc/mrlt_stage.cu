@@ -1,34 +1,16 @@
 // mrlt_stage.cu -- stage launch dispatch by equation, and the CFL wave-speed
 // reduction.  The stage kernels themselves are in mrlt_stage.cuh, instantiated
 // per equation by mrlt_stage_eq.cu.
-#include "mrlt_stage.cuh"
+#include "mrlt_macro.cuh"
 
 namespace mrlt {
 
 // largest sum of characteristic speeds over the leaves of level l (CFL step)
 template <int EQ, int D>
-__global__ void __launch_bounds__(NTHREADS) k_wave(Grid g, int l)
+__global__ void __launch_bounds__(NTHREADS) k_wave(const __grid_constant__ Grid g, int l)
 {
     pdl_enter();
-    constexpr int M = EQ == 2 ? D + 2 : 1;
-    const int cnt = g.counts[l];
-    const int* list = g.leaves + g.off[l];
-    const long long N = g.N[l];
-    double w = 0.0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
-        const long long id = list[t];
-        if (id < 0 || id >= N) continue;
-        const double* qe = fbase(g, F_QE, l) + id;
-        double q[M];
-#pragma unroll
-        for (int v = 0; v < M; ++v) q[v] = qe[v * N];
-        const double s = wave_speed<EQ, D, M>(g, q);
-        w = fmax(w, s != s ? 1e300 : s);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
-    if ((threadIdx.x & 31) == 0 && w > 0.0)
-        atomicMax(g.wmax, (unsigned long long)__double_as_longlong(w));
+    dev_wave<EQ, D>(g, l, l);
 }
 
 int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg)
@@ -40,6 +22,33 @@ int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin
     case 3: return launch_stage_eq<3>(g, st, lo, hi, s, lmin, b, reg);
     default: return 0;
     }
+}
+
+int launch_macro(const Grid& g, cudaStream_t st, const MacroArgs* a)
+{
+    switch (g.eq) {
+    case 0: return launch_macro_eq<0>(g, st, a);
+    case 1: return launch_macro_eq<1>(g, st, a);
+    case 2: return launch_macro_eq<2>(g, st, a);
+    case 3: return launch_macro_eq<3>(g, st, a);
+    default: return -1;
+    }
+}
+
+// Self-test of the bounded grid barrier: `ctas` CTAs wait at one barrier
+// that expects ctas + missing arrivals.  With missing > 0 nobody releases it:
+// every CTA gives up after limit_ns and ERR_TIMEOUT is set in *err.
+__global__ void k_grid_wait_test(unsigned* bar, int* err, unsigned long long limit_ns, unsigned missing)
+{
+    unsigned gen = 0;
+    grid_sync(bar, gen, err, limit_ns, gridDim.x + missing);
+}
+
+int launch_grid_wait_test(cudaStream_t st, int ctas, int missing, unsigned long long limit_ns, unsigned* bar,
+                          int* err)
+{
+    k_grid_wait_test<<<ctas, 32, 0, st>>>(bar, err, limit_ns, (unsigned)missing);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 void launch_wave(const Grid& g, cudaStream_t st, int l)

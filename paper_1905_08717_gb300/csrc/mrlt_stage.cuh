@@ -75,7 +75,17 @@ struct TileShape {
     static constexpr int NFY = D > 1 ? TX * (TY + 1) * TZ : 0;
     static constexpr int NFZ = D > 2 ? TX * TY * (TZ + 1) : 0;
     static constexpr int NF = NFX + NFY + NFZ;
-    static constexpr size_t SMEM = sizeof(double) * M * NB + sizeof(R) * M * NB + sizeof(R) * M * NF;
+    // parent-level block: the cells of level u-1 whose exposures predict the
+    // virtual cells of the block (Eq. 4 reads a 3^d neighbourhood of the parent)
+    static constexpr int PBX = TX / 2 + 4, PBY = D > 1 ? TY / 2 + 4 : 1, PBZ = D > 2 ? TZ / 2 + 4 : 1;
+    static constexpr int PB = PBX * PBY * PBZ;
+    // sub-face tasks whose two finer-side cells are fetched with the exposures
+    static constexpr int NPF = D > 2 ? 64 : NT;
+    // dynamic shared memory: conservative values of the block, of the parent
+    // block and q^n of the tile (double), reconstruction variables, face
+    // fluxes and the prefetched finer-side variables (R)
+    static constexpr size_t SMEM = sizeof(double) * M * (NB + PB + NC) +
+                                   sizeof(R) * M * (NB + NF + 2 * NPF);
 };
 
 // Append, in thread order, `item` to list A where `ta` holds and to list B
@@ -115,41 +125,118 @@ __device__ __forceinline__ void block_append2(bool ta, bool tb, int item, short*
     par ^= 1;
 }
 
-// Tiled stage (d = 1, 2, 3).  The CTA
-//  1. reads the status of its tile and a 2-cell ring; tiles without leaves exit;
-//  2. lists the cells some leaf of the tile reads -- its radius-2 cross stencil,
-//     plus the 3^d block of a leaf facing an internal node -- and stages their
-//     exposures (Secs. 4.1-4.3) and reconstruction variables in shared memory,
-//     stored nodes first, then virtual cells and ghosts;
-//  3. lists the faces touching a tile leaf and computes each once: plain faces
-//     on level u from the shared cells; faces of a leaf against an internal node
-//     as the mean of 2^{d-1} sub-face fluxes on level u+1 (Sec. 2), one thread
-//     per sub-face (the 2^{d-1} threads of a face are adjacent lanes), the
-//     leaf's virtual children predicted (Eq. 4) from its shared 3^d block and
-//     the finer side read from level u+1;
-//  4. applies the compact RK update and the register epilogue to its leaves.
-// Work lists keep every warp on one kind of work.
-template <int EQ, int D, class R>
-__global__ void __launch_bounds__(Tile<D>::THREADS)
-k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
+// Value of the stored finer-level node at in-box coordinates q of level l =
+// u + 1 as the level-u stencil sees it at stage x.s (the rel = +1 rows of
+// expose()), with its status and every field the choice may need loaded at
+// once: one memory round trip instead of status, then fields.  Returns false
+// (out untouched) when the cell is absent.
+template <int M>
+__device__ __forceinline__ bool finer_exposure(const Grid& g, const Ctx& x, int l, const int q[3], double* out)
 {
-    pdl_enter();
+    const long long id = cell_id(g, l, q[0], q[1], q[2]);
+    const long long N = g.N[l];
+    const double* q0 = fbase(g, F_Q0, l) + id;
+    const int st = status(g, l, id);
+    if (x.s <= 1) {
+        double a[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) a[v] = q0[v * N];
+        if (st == 0) return false;
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[v] = a[v];
+        return true;
+    }
+    if (g.gts || x.s == 3) { // global step: q* / q**; LT stage 3: q^{n+1} of the first sub-step
+        const double* a = fbase(g, g.gts ? (x.s == 2 ? F_Q1 : F_Q2) : F_QE, l) + id;
+        double b[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) b[v] = a[v * N];
+        if (st == 0) return false;
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[v] = b[v];
+        return true;
+    }
+    // LT stage 2: leaf Eq. 14 (q* + k2), internal node Eq. 15 (2 q* - q^n)
+    const double* q1 = fbase(g, F_Q1, l) + id;
+    const double* qx = fbase(g, g.rk == 2 ? F_QE : F_Q2, l) + id;
+    double a0[M], a1[M], ax[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        a0[v] = q0[v * N];
+        a1[v] = q1[v * N];
+        ax[v] = qx[v * N];
+    }
+    if (st == 0) return false;
+    if (st == 1) {
+        if (g.rk == 2) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = 2.0 * ax[v] - a0[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < M; ++v) out[v] = 4.0 * ax[v] - 3.0 * a0[v];
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < M; ++v) out[v] = 2.0 * a1[v] - a0[v];
+    }
+    return true;
+}
+
+// Tiled stage (d = 1, 2, 3).  The CTA works on one tile of one level at a
+// time, in phases separated by CTA barriers, with as few dependent trips to
+// memory as the data allow:
+//  1. status of the tile, its 2-cell ring and the parent-level block (one
+//     trip); tiles without leaves are skipped;
+//  2. lists, from the statuses alone: the cells some tile leaf reads -- its
+//     radius-2 cross stencil and the 3^d block of a leaf facing an internal
+//     node -- split into stored nodes and virtual cells (absent nodes and
+//     ghosts past a wall); the parent-block cells the virtual cells'
+//     predictions (Eq. 4) read; the faces touching a tile leaf, split into
+//     faces against an internal node (2^{d-1} sub-faces on level u+1, Sec. 2)
+//     and plain faces;
+//  3. one trip for everything the stage reads from memory: exposures
+//     (Secs. 4.1-4.3) of the stored cells and of the parent-block cells, the
+//     finer-side cells of the sub-faces, and q^n of the tile's leaves;
+//  4. virtual cells predicted in shared memory from the parent block (a ghost
+//     whose mirror image is stored takes that image's value);
+//  5. every face touching a tile leaf computed once, one thread per face or
+//     sub-face (the 2^{d-1} threads of a face are adjacent lanes, combined by
+//     shuffles), the leaf's own virtual children predicted from its shared
+//     3^d block;
+//  6. the compact RK update and the flux-register epilogue of the tile's leaves.
+// Work lists keep every warp on one kind of work.  Each value is computed by
+// the same operations in the same order as the direct definitions (expose,
+// predict, value_at); only the place its inputs come from changes.
+// The tiles of levels lo..hi are distributed over the CTAs of the launch
+// (blockIdx / gridDim); smem is the dynamic shared memory of TileShape::SMEM
+// bytes.  Called by k_stage_tile and by the persistent macro-step kernel.
+template <int EQ, int D, class R>
+__device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s, int lmin, double bstage, int reg,
+                                            unsigned char* smem)
+{
     const double dt = *g.dtp; // fine step of the macro step
     using S = TileShape<EQ, D, R>;
-    constexpr int M = S::M, TX = S::TX, TY = S::TY, TZ = S::TZ, NT = S::NT, H = S::H;
-    constexpr int BX = S::BX, BY = S::BY, NB = S::NB;
+    constexpr int M = S::M, TX = S::TX, TY = S::TY, TZ = S::TZ, NT = S::NT, H = S::H, NC = S::NC;
+    constexpr int BX = S::BX, BY = S::BY, BZ = S::BZ, NB = S::NB;
     constexpr int NFX = S::NFX, NFY = S::NFY, NF = S::NF;
+    constexpr int PBX = S::PBX, PBY = S::PBY, PBZ = S::PBZ, PB = S::PB, NPF = S::NPF;
     constexpr int NTS = 1 << (D - 1); // sub-faces per face
-    constexpr int NL = NB > NF ? NB : NF;
     constexpr int OUT = 3;            // status code of a cell past a wall
-    constexpr int SY = BX, SZ = BX * BY; // block strides in y and z
-    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int SY = BX, SZ = BX * BY;     // block strides in y and z
+    constexpr int PSY = PBX, PSZ = PBX * PBY; // parent-block strides
     double (*sW)[NB] = reinterpret_cast<double (*)[NB]>(smem);
-    R (*sP)[NB] = reinterpret_cast<R (*)[NB]>(smem + sizeof(double) * M * NB);
+    double (*sPW)[PB] = reinterpret_cast<double (*)[PB]>(smem + sizeof(double) * M * NB);
+    double (*sQ0)[NC] = reinterpret_cast<double (*)[NC]>(smem + sizeof(double) * M * (NB + PB));
+    unsigned char* rbase = smem + sizeof(double) * M * (NB + PB + NC);
+    R (*sP)[NB] = reinterpret_cast<R (*)[NB]>(rbase);
     // x faces [0, NFX), y faces [NFX, NFX + NFY), z faces [NFX + NFY, NF)
-    R (*sF)[NF] = reinterpret_cast<R (*)[NF]>(smem + (sizeof(double) + sizeof(R)) * M * NB);
-    __shared__ uint8_t sSt[NB];
-    __shared__ short sList[NL], sList2[NL];
+    R (*sF)[NF] = reinterpret_cast<R (*)[NF]>(rbase + sizeof(R) * M * NB);
+    R (*sFine)[M][NPF] = reinterpret_cast<R (*)[M][NPF]>(rbase + sizeof(R) * M * (NB + NF));
+    __shared__ uint8_t sSt[NB], sNeed[NB];  // status; needed | stored << 1
+    __shared__ uint8_t sPSt[PB], sPNeg[PB], sPNeed[PB];
+    __shared__ short sList[NB], sList2[NB]; // stored, virtual cells
+    __shared__ short sFace1[NF], sFace2[NF]; // faces against an internal node, plain faces
+    __shared__ short sPList[PB];
     __shared__ int sWarp[4 * (NT / 32)];
 
     // The CTA walks the active tiles (tiles holding a leaf) of levels lo..hi,
@@ -179,7 +266,10 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
     const int oz = D > 2 ? (tile / (ntx * nty)) * TZ : 0;
     const int tid = threadIdx.x;
     const Ctx x{u, s, lmin};
-    const bool finer = u < g.L; // internal nodes of level u have children
+    const bool finer = u < g.L;   // internal nodes of level u have children
+    const bool pstage = u > g.lb; // a parent level exists
+    // parent-block origin (level u-1 coordinates, before wrapping)
+    const int pox = (ox >> 1) - 2, poy = D > 1 ? (oy >> 1) - 2 : 0, poz = D > 2 ? (oz >> 1) - 2 : 0;
 
     // is block cell (bx, by, bz) a leaf of this tile?
     auto tile_leaf = [&](int bx, int by, int bz) -> bool {
@@ -241,8 +331,41 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
             leafHi = tile_leaf(H + i, H + j, H + kz);
         }
     };
+    // A virtual cell b: coordinates p (possibly past a wall); the in-box cell
+    // q that value_at() reads instead (wrapped or mirrored, neg = its value
+    // enters negated); the block cell bq holding q's status (-1: outside the
+    // block); the parent-block index pb0 of the corner of the 3^d
+    // neighbourhood whose exposures predict q (-1: outside the parent block).
+    // In a periodic direction the block cell itself holds the wrapped status,
+    // and the parent neighbourhood of p >> 1 wraps onto that of q >> 1.
+    auto resolve = [&](int b, int p[3], int q[3], int& neg, int& bq, int& pb0) {
+        const int bc3[3] = {b % BX, (b / BX) % BY, b / SZ};
+        const int o3[3] = {ox, oy, oz}, B3[3] = {BX, BY, BZ}, bs3[3] = {1, SY, SZ};
+        const int po3[3] = {pox, poy, poz}, P3[3] = {PBX, PBY, PBZ}, ps3[3] = {1, PSY, PSZ};
+        neg = 0;
+        bq = 0;
+        pb0 = 0;
+        bool inb = true, inp = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (k >= D) {
+                p[k] = q[k] = 0;
+                continue;
+            }
+            p[k] = o3[k] + bc3[k] - H;
+            q[k] = wrap_or_mirror(g, u, k, p[k], neg);
+            const int bk = g.bc[k] == 0 ? bc3[k] : q[k] - o3[k] + H;
+            inb = inb && bk >= 0 && bk < B3[k];
+            bq += bk * bs3[k];
+            const int pk = ((g.bc[k] == 0 ? p[k] : q[k]) >> 1) - 1 - po3[k];
+            inp = inp && pk >= 0 && pk + 2 < P3[k];
+            pb0 += pk * ps3[k];
+        }
+        if (!inb) bq = -1;
+        if (!inp || !pstage) pb0 = -1;
+    };
 
-    // 1. status of the tile and its ring
+    // 1. status of the tile, its ring and the parent-level block
     for (int b = tid; b < NB; b += NT) {
         const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
         int qx, qy = 0, qz = 0;
@@ -250,52 +373,35 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
                          (D < 3 || in_box(g, u, 2, oz + bz - H, &qz));
         sSt[b] = inb ? status(g, u, cell_id(g, u, qx, qy, qz)) : OUT;
     }
+    if (pstage)
+        for (int pb = tid; pb < PB; pb += NT) {
+            const int i = pb % PBX, j = (pb / PBX) % PBY, kk = pb / PSZ;
+            int neg = 0;
+            const int px = wrap_or_mirror(g, u - 1, 0, pox + i, neg);
+            const int py = D > 1 ? wrap_or_mirror(g, u - 1, 1, poy + j, neg) : 0;
+            const int pz = D > 2 ? wrap_or_mirror(g, u - 1, 2, poz + kk, neg) : 0;
+            sPSt[pb] = status(g, u - 1, cell_id(g, u - 1, px, py, pz));
+            sPNeg[pb] = (uint8_t)neg;
+            sPNeed[pb] = 0;
+        }
     __syncthreads();
     const int nleaf = __syncthreads_count(
-        tid < S::NC && tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0));
+        tid < NC && tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0));
     if (nleaf == 0) continue; // uniform across the CTA
     if (tid == 0) {
         if (s == 1) atomicAdd(g.updates, (unsigned long long)nleaf);
         atomicAdd(&g.work[u * 4 + s], (unsigned long long)nleaf);
     }
 
-    // 2. exposures of the needed cells: stored nodes (list 1), then virtual
-    //    cells and ghosts (list 2)
+    // 2. lists: stored and virtual needed cells, parent cells, faces
     int nst = 0, nvc = 0, par = 0;
     for (int b0 = 0; b0 < NB; b0 += NT) {
         const int b = b0 + tid;
         const bool nd = b < NB && needed(b);
         const bool stored = nd && (sSt[b] == 1 || sSt[b] == 2);
+        if (b < NB) sNeed[b] = (uint8_t)(nd | (stored << 1));
         block_append2<NT>(stored, nd && !stored, b, sList, sList2, nst, nvc, sWarp, par);
     }
-    __syncthreads();
-    for (int t = tid; t < nst + nvc; t += NT) {
-        const int b = t < nst ? sList[t] : sList2[t - nst];
-        const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
-        double W[M];
-        R P[M];
-        if (t < nst) {
-            int qx, qy = 0, qz = 0;
-            in_box(g, u, 0, ox + bx - H, &qx);
-            if (D > 1) in_box(g, u, 1, oy + by - H, &qy);
-            if (D > 2) in_box(g, u, 2, oz + bz - H, &qz);
-            expose<M>(g, x, u, cell_id(g, u, qx, qy, qz), sSt[b], W);
-        } else {
-            const int p[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, D > 2 ? oz + bz - H : 0};
-            value_at<D, M>(g, x, u, p, W);
-        }
-        recon_vars<EQ, D, M, R>(g, W, P);
-#pragma unroll
-        for (int v = 0; v < M; ++v) {
-            sW[v][b] = W[v];
-            sP[v][b] = P[v];
-        }
-    }
-    __syncthreads();
-
-    // 3. the faces touching a tile leaf, one pass: faces of a leaf against an
-    //    internal node (list 1, 2^{d-1} sub-face tasks each, in adjacent
-    //    lanes), then plain faces on level u (list 2), one thread per face
     int nsb = 0, nfl = 0;
     for (int f0 = 0; f0 < NF; f0 += NT) {
         const int f = f0 + tid;
@@ -307,14 +413,170 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
             sub = finer && ((lL && sSt[hi] == 2) || (lH && sSt[lo] == 2));
             plain = (lL || lH) && !sub;
         }
-        block_append2<NT>(sub, plain, f, sList, sList2, nsb, nfl, sWarp, par);
+        block_append2<NT>(sub, plain, f, sFace1, sFace2, nsb, nfl, sWarp, par);
+    }
+    __syncthreads(); // virtual list complete: mark the parent cells it reads
+    for (int t = tid; t < nvc; t += NT) {
+        int p[3], q[3], neg, bq, pb0;
+        resolve(sList2[t], p, q, neg, bq, pb0);
+        if (bq >= 0 && sSt[bq] == 0 && pb0 >= 0)
+#pragma unroll
+            for (int dz = 0; dz < (D > 2 ? 3 : 1); ++dz)
+#pragma unroll
+                for (int dy = 0; dy < (D > 1 ? 3 : 1); ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) sPNeed[pb0 + dz * PSZ + dy * PSY + dx] = 1;
+    }
+    __syncthreads();
+    int npl = 0, nnone = 0;
+    if (pstage) {
+        for (int p0 = 0; p0 < PB; p0 += NT) {
+            const int pb = p0 + tid;
+            block_append2<NT>(pb < PB && sPNeed[pb], false, pb, sPList, sPList, npl, nnone, sWarp, par);
+        }
     }
     __syncthreads();
     const int nsub = nsb * NTS; // sub-face tasks come first; NTS divides 32
+
+    // 3. one trip: exposures of stored and parent cells, finer-side cells of
+    //    the first sub-face tasks, q^n of the tile's leaves
+    double q0r[M];
+    const bool own_leaf = s >= 2 && tid < NC &&
+                          tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0);
+    if (own_leaf) {
+        const long long N = g.N[u];
+        const double* q0 = fbase(g, F_Q0, u) + cell_id(g, u, ox + tid % TX, D > 1 ? oy + (tid / TX) % TY : 0,
+                                                       D > 2 ? oz + tid / (TX * TY) : 0);
+#pragma unroll
+        for (int v = 0; v < M; ++v) q0r[v] = q0[v * N];
+    }
+    for (int t = tid; t < nst + npl; t += NT) {
+        double W[M];
+        if (t < nst) {
+            const int b = sList[t];
+            const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
+            int qx, qy = 0, qz = 0;
+            in_box(g, u, 0, ox + bx - H, &qx);
+            if (D > 1) in_box(g, u, 1, oy + by - H, &qy);
+            if (D > 2) in_box(g, u, 2, oz + bz - H, &qz);
+            expose<M>(g, x, u, cell_id(g, u, qx, qy, qz), sSt[b], W);
+            R P[M];
+            recon_vars<EQ, D, M, R>(g, W, P);
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+                sW[v][b] = W[v];
+                sP[v][b] = P[v];
+            }
+        } else {
+            const int pb = sPList[t - nst];
+            const int st = sPSt[pb];
+            if (st == 0) continue; // predict() flags the absent source when it reads it
+            const int i = pb % PBX, j = (pb / PBX) % PBY, kk = pb / PSZ;
+            int neg = 0;
+            const int px = wrap_or_mirror(g, u - 1, 0, pox + i, neg);
+            const int py = D > 1 ? wrap_or_mirror(g, u - 1, 1, poy + j, neg) : 0;
+            const int pz = D > 2 ? wrap_or_mirror(g, u - 1, 2, poz + kk, neg) : 0;
+            expose<M>(g, x, u - 1, cell_id(g, u - 1, px, py, pz), st, W);
+            // an odd-mirror ghost enters negated: (-w) v = w (-v) exactly
+#pragma unroll
+            for (int v = 0; v < M; ++v) sPW[v][pb] = neg ? -W[v] : W[v];
+        }
+    }
+    if (tid < nsub && tid < NPF) { // sub-face task tid: its two finer-side cells
+        const int f = sFace1[tid / NTS], t = tid % NTS;
+        int k, lo, hi;
+        bool lL, lH;
+        face(f, k, lo, hi, lL, lH);
+        const bool leafIsLo = lL && sSt[hi] == 2;
+        const int bl = leafIsLo ? lo : hi, side = leafIsLo ? 1 : -1;
+        const int bx = bl % BX, by = (bl / BX) % BY, bz = bl / SZ;
+        const int c[3] = {ox + bx - H, D > 1 ? oy + by - H : 0, D > 2 ? oz + bz - H : 0};
+        const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int i = side > 0 ? 2 + r : r; // the cells on the internal node's side
+            int p[3] = {0, 0, 0};
+            p[k] = 2 * c[k] + (side > 0 ? i : i - 2);
+            if (D > 1) p[j1] = 2 * c[j1] + (t & 1);
+            if (D > 2) p[j2] = 2 * c[j2] + (t >> 1);
+            int q[3] = {0, 0, 0}, neg = 0;
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) q[kk] = wrap_or_mirror(g, u + 1, kk, p[kk], neg);
+            double W[M];
+            if (!finer_exposure<M>(g, x, u + 1, q, W)) {
+                value_at<D, M>(g, x, u + 1, p, W); // absent: predicted (flags the missing source)
+            } else if (neg) {
+#pragma unroll
+                for (int v = 0; v < M; ++v) W[v] = -W[v];
+            }
+            R P[M];
+            recon_vars<EQ, D, M, R>(g, W, P);
+#pragma unroll
+            for (int v = 0; v < M; ++v) sFine[r][v][tid] = P[v];
+        }
+    }
+    if (own_leaf)
+#pragma unroll
+        for (int v = 0; v < M; ++v) sQ0[v][tid] = q0r[v];
+    __syncthreads();
+
+    // 4. virtual cells: predicted from the parent block (the terms of
+    //    predict() in its order), or a stored mirror image, else value_at()
+    for (int t = tid; t < nvc; t += NT) {
+        const int b = sList2[t];
+        int p[3], q[3], neg, bq, pb0;
+        resolve(b, p, q, neg, bq, pb0);
+        double W[M];
+        if (bq >= 0 && sSt[bq] == 0 && pb0 >= 0) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) W[v] = 0.0;
+            const int a0 = q[0] & 1, a1 = q[1] & 1, a2 = q[2] & 1;
+#pragma unroll(D > 2 ? 1 : 3)
+            for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
+                const double wz = D > 2 ? pw(a2, dz) : 1.0;
+#pragma unroll(D > 2 ? 1 : 3)
+                for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
+                    const double wyz = wz * (D > 1 ? pw(a1, dy) : 1.0);
+#pragma unroll
+                    for (int dxx = -1; dxx <= 1; ++dxx) {
+                        const int pb = pb0 + (D > 2 ? (dz + 1) * PSZ : 0) + (D > 1 ? (dy + 1) * PSY : 0) + dxx + 1;
+                        if (sPSt[pb] == 0) {
+                            atomicOr(g.err, ERR_SOURCE);
+                            continue;
+                        }
+                        const double w0 = wyz * pw(a0, dxx);
+#pragma unroll
+                        for (int v = 0; v < M; ++v) W[v] += w0 * sPW[v][pb];
+                    }
+                }
+            }
+            if (neg) {
+#pragma unroll
+                for (int v = 0; v < M; ++v) W[v] = -W[v];
+            }
+        } else if (bq >= 0 && (sNeed[bq] & 2)) { // a ghost whose mirror image is a staged stored cell
+#pragma unroll
+            for (int v = 0; v < M; ++v) W[v] = neg ? -sW[v][bq] : sW[v][bq];
+        } else {
+            value_at<D, M>(g, x, u, p, W);
+        }
+        R P[M];
+        recon_vars<EQ, D, M, R>(g, W, P);
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            sW[v][b] = W[v];
+            sP[v][b] = P[v];
+        }
+    }
+    __syncthreads();
+
+    // 5. the faces touching a tile leaf, one pass: faces of a leaf against an
+    //    internal node (2^{d-1} sub-face tasks each, in adjacent lanes), then
+    //    plain faces on level u, one thread per face
     for (int base = 0; base < nsub + nfl; base += NT) {
         const int task = base + tid;
         const bool isSub = task < nsub, act = task < nsub + nfl;
-        const int f = isSub ? sList[task / NTS] : (act ? sList2[task - nsub] : 0);
+        const int f = isSub ? sFace1[task / NTS] : (act ? sFace2[task - nsub] : 0);
         const int t = isSub ? task % NTS : 0;
         R F[M];
 #pragma unroll
@@ -335,6 +597,7 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
                 // tangential directions of the face, in increasing order; sub-face
                 // t takes child offset (t & 1) along the first, (t >> 1) along the second
                 const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+                const bool pre = task < NPF; // finer side fetched in phase 3
                 R P4[4][M];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -344,8 +607,8 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
                     if (D > 1) p[j1] = 2 * c[j1] + (t & 1);
                     if (D > 2) p[j2] = 2 * c[j2] + (t >> 1);
                     const bool own = side > 0 ? i < 2 : i >= 2;
-                    double W[M];
                     if (own) {
+                        double W[M];
                         const int ax = p[0] & 1, ay = p[1] & 1, az = p[2] & 1;
 #pragma unroll
                         for (int v = 0; v < M; ++v) W[v] = 0.0;
@@ -361,10 +624,16 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
 #pragma unroll
                                     for (int v = 0; v < M; ++v) W[v] += w * sW[v][bs];
                                 }
+                        recon_vars<EQ, D, M, R>(g, W, P4[i]);
+                    } else if (pre) {
+                        const int r = side > 0 ? i - 2 : i;
+#pragma unroll
+                        for (int v = 0; v < M; ++v) P4[i][v] = sFine[r][v][task];
                     } else {
+                        double W[M];
                         value_at<D, M>(g, x, u + 1, p, W);
+                        recon_vars<EQ, D, M, R>(g, W, P4[i]);
                     }
-                    recon_vars<EQ, D, M, R>(g, W, P4[i]);
                 }
                 flux_recon<EQ, D, M, R>(g, k, g.dx[u + 1][k], [&](int cc, int v) { return P4[cc][v]; }, F);
             }
@@ -393,8 +662,8 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
     }
     __syncthreads();
 
-    // 4. compact RK update of the tile's leaves (thread tid < NC owns cell tid)
-    if (tid < S::NC) {
+    // 6. compact RK update of the tile's leaves (thread tid < NC owns cell tid)
+    if (tid < NC) {
         const int i = tid % TX, j = D > 1 ? (tid / TX) % TY : 0, kz = D > 2 ? tid / (TX * TY) : 0;
         const int bx = H + i, by = D > 1 ? H + j : 0, bz = D > 2 ? H + kz : 0;
         const int b = bz * SZ + by * SY + bx;
@@ -403,15 +672,8 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
         double self[M], f[M], q0p[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) self[v] = sW[v][b];
-        if (s >= 2) { // q^n (the stage value itself is the staged exposure)
-            const long long N = g.N[u];
-            const double* q0 = fbase(g, F_Q0, u) + id;
 #pragma unroll
-            for (int v = 0; v < M; ++v) q0p[v] = q0[v * N];
-        } else {
-#pragma unroll
-            for (int v = 0; v < M; ++v) q0p[v] = self[v];
-        }
+        for (int v = 0; v < M; ++v) q0p[v] = s >= 2 ? sQ0[v][tid] : self[v]; // the stage value is the staged exposure
         source<EQ, M>(g, self, f);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -450,6 +712,15 @@ k_stage_tile(Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
     }
     __syncthreads(); // shared arrays are reused by the next tile
     }
+}
+
+template <int EQ, int D, class R>
+__global__ void __launch_bounds__(Tile<D>::THREADS)
+k_stage_tile(const __grid_constant__ Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
+{
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_tiles<EQ, D, R>(g, lo, hi, s, lmin, bstage, reg, smem);
 }
 
 static inline int grid_for(const Grid& g, int l)

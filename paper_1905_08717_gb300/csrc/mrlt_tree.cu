@@ -18,613 +18,104 @@ static inline int blocks_list(const Grid& g, int l)
     return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
 }
 
-#define GRID_STRIDE(i, n) \
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+#define GRID_STRIDE(i, n) MRLT_GRID_STRIDE(i, n)
 
-// ------------------------------------------------------------ simple leaf copies
-__global__ void k_leaf_copy(Grid g, int lo, int hi, int from, int to)
+// ------------------------------------------------------------ kernels
+// Each kernel waits for its predecessor (programmatic dependent launch) and
+// runs one device body of mrlt_tree_dev.cuh over its own grid.
+__global__ void k_leaf_copy(const __grid_constant__ Grid g, int lo, int hi, int from, int to)
 {
     pdl_enter();
-    for (int l = lo; l <= hi; ++l) {
-        const int cnt = g.counts[l];
-        const int* list = g.leaves + g.off[l];
-        const long long N = g.N[l];
-        const double* a = fbase(g, from, l);
-        double* b = fbase_w(g, to, l);
-        GRID_STRIDE(t, cnt)
-        {
-            const long long id = list[t];
-            if (id < 0 || id >= N) {
-                atomicOr(g.err, ERR_INDEX);
-                continue;
-            }
-            for (int v = 0; v < g.m; ++v) b[v * N + id] = a[v * N + id];
-        }
-    }
+    dev_leaf_copy(g, lo, hi, from, to);
 }
 
-// ------------------------------------------------------------ projections
-// Every internal node of level l combines its 2^d children (Eq. 3 mean):
-//  PM_Q0 / PM_Q1 / PM_Q2: plain projection of that field (Alg. 3; GTS stages)
-//  PM_REF2: Alg. 8 -- XH = mean q* (Eq. 17), q* = 2 XH - q^n (Eq. 18)
-//  PM_PRJ2: Alg. 4 -- q* = mean(leaf: Eq. 14 value, internal: Eq. 15 value)
-//  PM_REF3: Alg. 9 -- N1 = mean q**, N3 by Eq. 20, q** by Eq. 21
-//  PM_PRJ3: Alg. 6 -- q** = mean(children at t^n + dt_{l+1}), end value
-//           2 q** - q^n (Eq. 16 with the theta values implied by q**)
-//  PM_MID:  Alg. 3 / Sec. 4.3 refresh of the mid-step level lmin-1
 template <int D>
-__global__ void k_project(Grid g, int l, int mode)
+__global__ void k_project(const __grid_constant__ Grid g, int l, int mode)
 {
     pdl_enter();
-    const int cnt = g.counts[LMAX + 1 + l];
-    const int* list = g.inner + g.off[l];
-    const long long N = g.N[l], Nc = g.N[l + 1];
-    constexpr int NCH = 1 << D;
-    GRID_STRIDE(t, cnt)
-    {
-        const long long id = list[t];
-        if (id < 0 || id >= N) {
-            atomicOr(g.err, ERR_INDEX);
-            continue;
-        }
-        int c[3];
-        cell_xyz(g, l, id, c);
-        long long ch[NCH];
-        uint8_t cst[NCH];
-#pragma unroll
-        for (int k = 0; k < NCH; ++k) {
-            ch[k] = cell_id(g, l + 1, 2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
-                            D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
-            cst[k] = status(g, l + 1, ch[k]);
-        }
-        const double* c0 = fbase(g, F_Q0, l + 1);
-        const double* c1 = fbase(g, F_Q1, l + 1);
-        const double* c2 = fbase(g, F_Q2, l + 1);
-        const double* ce = fbase(g, F_QE, l + 1);
-        double* q0 = fbase_w(g, F_Q0, l);
-        double* q1 = fbase_w(g, F_Q1, l);
-        double* q2 = fbase_w(g, F_Q2, l);
-        double* qe = fbase_w(g, F_QE, l);
-        for (int v = 0; v < g.m; ++v) {
-            const long long o = v * N + id;
-            double acc = 0.0;
-#pragma unroll
-            for (int k = 0; k < NCH; ++k) {
-                const long long oc = v * Nc + ch[k];
-                double w;
-                switch (mode) {
-                case PM_Q0: w = c0[oc]; break;
-                case PM_Q1: case PM_REF2: w = c1[oc]; break;
-                case PM_Q2: case PM_REF3: w = c2[oc]; break;
-                case PM_PRJ2:
-                    if (cst[k] == 1) w = g.rk == 2 ? 2.0 * ce[oc] - c0[oc] : 4.0 * c2[oc] - 3.0 * c0[oc];
-                    else w = 2.0 * c1[oc] - c0[oc];
-                    break;
-                case PM_PRJ3: w = ce[oc]; break;
-                default: w = c0[oc]; break; // PM_MID: children at t^n
-                }
-                acc += w;
-            }
-            const double mean = acc * (1.0 / NCH);
-            switch (mode) {
-            case PM_Q0: q0[o] = mean; break;
-            case PM_Q1: case PM_PRJ2: q1[o] = mean; break;
-            case PM_Q2: q2[o] = mean; break;
-            case PM_REF2:
-                fbase_w(g, F_XH, l)[o] = mean;
-                q1[o] = 2.0 * mean - q0[o];
-                break;
-            case PM_REF3: {
-                fbase_w(g, F_N1, l)[o] = mean;
-                fbase_w(g, F_N3, l)[o] = -6.5 * q0[o] - 1.5 * q1[o] + 9.0 * mean;
-                q2[o] = -5.5 * q0[o] - 1.5 * q1[o] + 8.0 * mean;
-                break;
-            }
-            case PM_PRJ3:
-                q2[o] = mean;
-                qe[o] = 2.0 * mean - q0[o];
-                break;
-            default: { // PM_MID
-                if (g.rk == 2) {
-                    fbase_w(g, F_NH, l)[o] = mean;
-                    qe[o] = -2.0 * q0[o] - q1[o] + 4.0 * mean;
-                } else {
-                    q2[o] = mean;
-                    qe[o] = 2.0 * mean - q0[o];
-                    const double n1 = (mean + 5.5 * q0[o] + 1.5 * q1[o]) * 0.125;
-                    fbase_w(g, F_N1, l)[o] = n1;
-                    fbase_w(g, F_N3, l)[o] = -6.5 * q0[o] - 1.5 * q1[o] + 9.0 * n1;
-                }
-            }
-            }
-        }
-    }
+    dev_project<D>(g, l, mode);
 }
 
-// ------------------------------------------------------------ adaptation
-__device__ __forceinline__ double eps_level(const Grid& g, int l)
-{
-    return g.eps_mode == 1 ? ldexp(g.eps, g.d * (l - g.L)) : g.eps;
-}
-
-// detail norm (Eq. 5) of every internal node of levels lo..hi (< L): max over
-// children and variables of |q_child - prediction| / s_v; flags significance
-// (> eps_{l+1}) and the scale-safety bound (> 8 eps_{l+1})
 template <int D, int M>
-__global__ void k_detail(Grid g, int lo, int hi)
+__global__ void k_detail(const __grid_constant__ Grid g, int lo, int hi)
 {
     pdl_enter();
-    double sc[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) sc[v] = __longlong_as_double((long long)g.scale_bits[v]);
-    for (int l = lo; l <= hi; ++l) {
-        const int cnt = g.counts[LMAX + 1 + l];
-        const int* list = g.inner + g.off[l];
-        const long long N = g.N[l], Nc = g.N[l + 1];
-        const double el = eps_level(g, l + 1);
-        GRID_STRIDE(t, cnt)
-        {
-            const long long id = list[t];
-            if (id < 0 || id >= N) {
-                atomicOr(g.err, ERR_INDEX);
-                continue;
-            }
-            uint8_t fl = 0;
-            if (g.eps <= 0.0) {
-                fl = FL_SIG;
-            } else {
-                int c[3];
-                cell_xyz(g, l, id, c);
-                const Ctx x{l, 0, g.lb};
-                double nrm = 0.0;
-#pragma unroll 1
-                for (int k = 0; k < (1 << D); ++k) {
-                    int q[3] = {2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
-                                D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0};
-                    double p[M];
-                    predict<D, M>(g, x, l + 1, q, p);
-                    const long long cid = cell_id(g, l + 1, q[0], q[1], q[2]);
-                    const double* qc = fbase(g, F_Q0, l + 1) + cid;
-#pragma unroll
-                    for (int v = 0; v < M; ++v) nrm = fmax(nrm, fabs(qc[v * Nc] - p[v]) / sc[v]);
-                }
-                if (fabs(nrm - el) <= 1e-10 * el || fabs(nrm - 8.0 * el) <= 8e-10 * el)
-                    atomicAdd(g.near, 1ull);
-                if (nrm > el) fl |= FL_SIG;
-                if (nrm > 8.0 * el) fl |= FL_BIG;
-            }
-            g.flag[g.off[l] + id] |= fl;
-        }
-    }
+    dev_detail<D, M>(g, lo, hi);
 }
 
 template <int D>
-__device__ __forceinline__ bool nb3(const Grid& g, int l, const int c[3], int dx, int dy, int dz, long long* id)
-{
-    int q[3] = {0, 0, 0};
-    if (!in_box(g, l, 0, c[0] + dx, &q[0])) return false;
-    if (D > 1 && !in_box(g, l, 1, c[1] + dy, &q[1])) return false;
-    if (D > 2 && !in_box(g, l, 2, c[2] + dz, &q[2])) return false;
-    *id = cell_id(g, l, q[0], q[1], q[2]);
-    return true;
-}
-
-#define FOR3(D, dx, dy, dz)                                       \
-    for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) \
-        for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) \
-            for (int dx = -1; dx <= 1; ++dx)
-
-// desired refinement of levels lo..hi: significant node in the 3^d
-// neighbourhood (space safety), or parent flagged by scale safety (parent
-// level >= la); eps = 0 refines all
-template <int D>
-__global__ void k_desire(Grid g, int lo, int hi, int la)
+__global__ void k_desire(const __grid_constant__ Grid g, int lo, int hi, int la)
 {
     pdl_enter();
-    for (int l = lo; l <= hi; ++l) {
-        const long long N = g.N[l];
-        uint8_t* fl = g.flag + g.off[l];
-        GRID_STRIDE(id, N)
-        {
-            bool want = g.eps <= 0.0;
-            if (!want) {
-                int c[3];
-                cell_xyz(g, l, id, c);
-                FOR3(D, dx, dy, dz)
-                {
-                    long long j;
-                    if (nb3<D>(g, l, c, dx, dy, dz, &j) && (fl[j] & FL_SIG)) want = true;
-                }
-                if (!want && l - 1 >= la) {
-                    const long long p = cell_id(g, l - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1);
-                    if (g.flag[g.off[l - 1] + p] & FL_BIG) want = true;
-                }
-            }
-            if (want) fl[id] |= FL_DES;
-        }
-    }
+    dev_desire<D>(g, lo, hi, la);
 }
 
-// Admissible refinements of levels lo..hi and R = desired and admissible.
-// A node (l, i) may be refined if every node of the frozen level la-1 its
-// grading chain requires is refined already.  Unrolling the rule "refining
-// (m, j) needs (m-1, floor(j/2) + delta), |delta| <= 1" from level l down to
-// la-1 gives, per direction, the interval [a, b] obtained by
-// a -> floor(a/2) - 1, b -> floor(b/2) + 1 (l - la + 1 times), wrapped when
-// periodic and clipped at walls.  At a full adaptation (la = min level)
-// everything is admissible.
 template <int D>
-__global__ void k_allow(Grid g, int lo, int hi, int la)
+__global__ void k_allow(const __grid_constant__ Grid g, int lo, int hi, int la)
 {
     pdl_enter();
-    for (int l = lo; l <= hi; ++l) {
-        const long long N = g.N[l];
-        uint8_t* fl = g.flag + g.off[l];
-        GRID_STRIDE(id, N)
-        {
-            bool ok = true;
-            if (la > g.lb) {
-                int c[3];
-                cell_xyz(g, l, id, c);
-                const int pl = la - 1, n = g.n[pl];
-                int lo3[3] = {0, 0, 0}, cnt3[3] = {1, 1, 1};
-                for (int k = 0; k < D; ++k) {
-                    int a = c[k], b = c[k];
-                    for (int m = l; m >= la; --m) {
-                        a = (a >> 1) - 1; // arithmetic shift: floor for negatives
-                        b = (b >> 1) + 1;
-                    }
-                    if (g.bc[k] == 0) {
-                        lo3[k] = a;
-                        cnt3[k] = min(b - a + 1, n);
-                    } else {
-                        lo3[k] = max(a, 0);
-                        cnt3[k] = min(b, n - 1) - lo3[k] + 1;
-                    }
-                }
-                for (int tz = 0; tz < cnt3[2] && ok; ++tz)
-                    for (int ty = 0; ty < cnt3[1] && ok; ++ty)
-                        for (int tx = 0; tx < cnt3[0] && ok; ++tx) {
-                            int q[3] = {lo3[0] + tx, lo3[1] + ty, lo3[2] + tz};
-                            for (int k = 0; k < D; ++k)
-                                if (g.bc[k] == 0) q[k] = ((q[k] % n) + n) % n;
-                            ok = status(g, pl, cell_id(g, pl, q[0], q[1], q[2])) == 2;
-                        }
-            }
-            uint8_t f = fl[id];
-            if (ok) {
-                f |= FL_ALLOW;
-                if (f & FL_DES) f |= FL_REF;
-            }
-            fl[id] = f;
-        }
-    }
+    dev_allow<D>(g, lo, hi, la);
 }
 
-// grading closure, one level: refining (l, i) refines (l-1, floor(i/2) + delta)
-// for |delta|_inf <= 1 -- gathered at the coarse node
 template <int D>
-__global__ void k_close(Grid g, int l)
+__global__ void k_close(const __grid_constant__ Grid g, int l)
 {
     pdl_enter();
-    const int pl = l - 1;
-    const long long N = g.N[pl];
-    uint8_t* fp = g.flag + g.off[pl];
-    const uint8_t* fc = g.flag + g.off[l];
-    GRID_STRIDE(pid, N)
-    {
-        if (fp[pid] & FL_REF) continue;
-        int c[3];
-        cell_xyz(g, pl, pid, c);
-        bool hit = false;
-        FOR3(D, dx, dy, dz)
-        {
-            long long j;
-            if (!nb3<D>(g, pl, c, -dx, -dy, -dz, &j)) continue;
-            int q[3];
-            cell_xyz(g, pl, j, q);
-            for (int k = 0; k < (1 << D); ++k) {
-                const long long cid = cell_id(g, l, 2 * q[0] + (k & 1), D > 1 ? 2 * q[1] + ((k >> 1) & 1) : 0,
-                                              D > 2 ? 2 * q[2] + ((k >> 2) & 1) : 0);
-                if (fc[cid] & FL_REF) hit = true;
-            }
-        }
-        if (hit) fp[pid] |= FL_REF;
-    }
+    dev_close<D>(g, l);
 }
 
-// install the new tree on level l (top-down): status from the refinement
-// flags; new nodes predicted from level l-1 (Sec. 2); new leaves and merged
-// nodes get q^{n+1} = q^n; registers of changed nodes cleared
 template <int D, int M>
-__global__ void k_apply(Grid g, int l, int la)
+__global__ void k_apply(const __grid_constant__ Grid g, int l, int la)
 {
     pdl_enter();
-    const long long N = g.N[l];
-    GRID_STRIDE(id, N)
-    {
-        const uint8_t old = status(g, l, id);
-        int c[3];
-        cell_xyz(g, l, id, c);
-        bool exists;
-        if (l == la) exists = old != 0;
-        else {
-            const long long p = cell_id(g, l - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1);
-            exists = (g.flag[g.off[l - 1] + p] & FL_REF) != 0;
-        }
-        const bool refined = l < g.L && (g.flag[g.off[l] + id] & FL_REF);
-        if (refined && !exists) atomicOr(g.err, ERR_SOURCE);
-        const uint8_t nw = exists ? (refined ? 2 : 1) : 0;
-        if (nw == old) continue;
-        g.st[g.off[l] + id] = nw;
-        double* q0 = fbase_w(g, F_Q0, l) + id;
-        if (old == 0 && nw != 0) {
-            const Ctx x{l, 0, g.lb};
-            double p[M];
-            predict<D, M>(g, x, l, c, p);
-#pragma unroll
-            for (int v = 0; v < M; ++v) q0[v * N] = p[v];
-        }
-        if (nw == 1) {
-            double* qe = fbase_w(g, F_QE, l) + id;
-#pragma unroll
-            for (int v = 0; v < M; ++v) qe[v * N] = q0[v * N];
-        }
-        if (g.rc) {
-            const long long roff = g.off[l] * g.nf * M;
-            for (int r = 0; r < g.nf * M; ++r) {
-                g.rc[roff + r * N + id] = 0.0;
-                g.rf[roff + r * N + id] = 0.0;
-            }
-        }
-    }
+    dev_apply<D, M>(g, l, la);
 }
 
-// ------------------------------------------------------------ compaction
-// Level l owns the blocks [lb.base[l], lb.base[l+1]) of a compaction launch
-// over levels lb.lo..lb.hi (NTHREADS cells per block).
-struct LevelBlocks {
-    int lo, hi;
-    int base[LMAX + 2];
-};
-
-__device__ __forceinline__ int block_level(const LevelBlocks& b, int blk)
-{
-    int l = b.lo;
-    while (l < b.hi && blk >= b.base[l + 1]) ++l;
-    return l;
-}
-
-__global__ void k_cmp_count(Grid g, LevelBlocks lbk, int* bc)
+// compaction of levels lo..hi: chunks of NTHREADS cells, one block each
+__global__ void k_cmp_count(const __grid_constant__ Grid g, LevelChunks lc, int* bc)
 {
     pdl_enter();
-    const int l = block_level(lbk, blockIdx.x);
-    const long long N = g.N[l];
-    const long long i = (long long)(blockIdx.x - lbk.base[l]) * blockDim.x + threadIdx.x;
-    const int s = i < N ? status(g, l, i) : 0;
-    const unsigned bl = __ballot_sync(0xffffffffu, s == 1);
-    const unsigned bi = __ballot_sync(0xffffffffu, s == 2);
-    __shared__ int wl[NTHREADS / 32], wi[NTHREADS / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        wl[warp] = __popc(bl);
-        wi[warp] = __popc(bi);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int a = 0, b = 0;
-        for (int w = 0; w < NTHREADS / 32; ++w) {
-            a += wl[w];
-            b += wi[w];
-        }
-        bc[2 * blockIdx.x] = a;
-        bc[2 * blockIdx.x + 1] = b;
-    }
+    chunk_count<NTHREADS>(g, lc, blockIdx.x, bc);
 }
 
-// exclusive scan of the per-block counts, one block per level; totals to counts[l]
-__global__ void k_cmp_scan(Grid g, LevelBlocks lbk, int* bc)
+// exclusive scan of the per-chunk counts, one block per level
+__global__ void k_cmp_scan(const __grid_constant__ Grid g, LevelChunks lc, int* bc)
 {
     pdl_enter();
-    __shared__ int sa[1024], sb[1024];
-    const int l = lbk.lo + blockIdx.x;
-    const int b0l = lbk.base[l], nb = lbk.base[l + 1] - b0l;
-    const int tid = threadIdx.x;
-    const int per = (nb + 1023) / 1024;
-    const int b0 = b0l + tid * per, b1 = min(b0 + per, b0l + nb);
-    int a = 0, b = 0;
-    for (int i = b0; i < b1; ++i) {
-        a += bc[2 * i];
-        b += bc[2 * i + 1];
-    }
-    sa[tid] = a;
-    sb[tid] = b;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int xa = tid >= o ? sa[tid - o] : 0;
-        const int xb = tid >= o ? sb[tid - o] : 0;
-        __syncthreads();
-        sa[tid] += xa;
-        sb[tid] += xb;
-        __syncthreads();
-    }
-    int ea = sa[tid] - a, eb = sb[tid] - b;
-    for (int i = b0; i < b1; ++i) {
-        const int ta = bc[2 * i], tb = bc[2 * i + 1];
-        bc[2 * i] = ea;
-        bc[2 * i + 1] = eb;
-        ea += ta;
-        eb += tb;
-    }
-    if (tid == 1023) {
-        g.counts[l] = sa[1023];
-        g.counts[LMAX + 1 + l] = sb[1023];
-    }
+    level_scan<1024>(g, lc, lc.lo + blockIdx.x, bc);
 }
 
-__global__ void k_cmp_scatter(Grid g, LevelBlocks lbk, const int* bc)
+__global__ void k_cmp_scatter(const __grid_constant__ Grid g, LevelChunks lc, const int* bc)
 {
     pdl_enter();
-    const int l = block_level(lbk, blockIdx.x);
-    const long long N = g.N[l];
-    const long long i = (long long)(blockIdx.x - lbk.base[l]) * blockDim.x + threadIdx.x;
-    const int s = i < N ? status(g, l, i) : 0;
-    const unsigned bl = __ballot_sync(0xffffffffu, s == 1);
-    const unsigned bi = __ballot_sync(0xffffffffu, s == 2);
-    __shared__ int wl[NTHREADS / 32], wi[NTHREADS / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        wl[warp] = __popc(bl);
-        wi[warp] = __popc(bi);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int a = bc[2 * blockIdx.x], b = bc[2 * blockIdx.x + 1];
-        for (int w = 0; w < NTHREADS / 32; ++w) {
-            const int ta = wl[w], tb = wi[w];
-            wl[w] = a;
-            wi[w] = b;
-            a += ta;
-            b += tb;
-        }
-    }
-    __syncthreads();
-    const unsigned below = (1u << lane) - 1u;
-    if (s == 1) g.leaves[g.off[l] + wl[warp] + __popc(bl & below)] = (int)i;
-    if (s == 2) g.inner[g.off[l] + wi[warp] + __popc(bi & below)] = (int)i;
-    if (s == 1) { // the leaf's tile is active
-        const long long n = g.n[l];
-        const int tx = g.d == 1 ? kTile1X : (g.d == 2 ? kTile2X : kTile3X);
-        const int ty = g.d == 2 ? kTile2Y : kTile3Y;
-        const long long x = i % n, y = g.d >= 2 ? (i / n) % n : 0, z = g.d == 3 ? i / (n * n) : 0;
-        g.tflag[g.toff[l] + x / tx + (long long)g.ntx[l] * (y / ty + (long long)g.nty[l] * (z / kTile3Z))] = 1;
-    }
+    chunk_scatter<NTHREADS>(g, lc, blockIdx.x, bc);
 }
 
 // ordered list of the active tiles of level lo + blockIdx.x (one block per level)
-__global__ void k_tile_list(Grid g, int lo)
+__global__ void k_tile_list(const __grid_constant__ Grid g, int lo)
 {
     pdl_enter();
-    __shared__ int sc[1024];
-    const int l = lo + blockIdx.x;
-    const int nt = g.ntx[l] * g.nty[l] * g.ntz[l];
-    const uint8_t* fl = g.tflag + g.toff[l];
-    const int tid = threadIdx.x, per = (nt + 1023) / 1024;
-    const int t0 = tid * per, t1 = min(t0 + per, nt);
-    int c = 0;
-    for (int t = t0; t < t1; ++t) c += fl[t] != 0;
-    sc[tid] = c;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int xo = tid >= o ? sc[tid - o] : 0;
-        __syncthreads();
-        sc[tid] += xo;
-        __syncthreads();
-    }
-    int pos = sc[tid] - c;
-    for (int t = t0; t < t1; ++t)
-        if (fl[t]) g.tlist[g.toff[l] + pos++] = t;
-    if (tid == 1023) g.counts[2 * (LMAX + 1) + l] = sc[1023];
+    level_tile_list<1024>(g, lo + blockIdx.x);
 }
 
-// ------------------------------------------------------------ registers
-// conservative correction of the coarse leaves of level l whose step ended:
-// q += +-(coarse time-integrated flux - mean of the fine ones) / dx; the
-// registers read are cleared for the next step
 template <int D>
-__global__ void k_reflux(Grid g, int lo, int hi)
+__global__ void k_reflux(const __grid_constant__ Grid g, int lo, int hi)
 {
     pdl_enter();
-  for (int l = lo; l <= hi; ++l) {
-    const int cnt = g.counts[l];
-    const int* list = g.leaves + g.off[l];
-    const long long N = g.N[l], Nf = g.N[l + 1];
-    const int m = g.m;
-    constexpr int NT = 1 << (D - 1);
-    GRID_STRIDE(t, cnt)
-    {
-        const long long id = list[t];
-        if (id < 0 || id >= N) {
-            atomicOr(g.err, ERR_INDEX);
-            continue;
-        }
-        int c[3];
-        cell_xyz(g, l, id, c);
-        for (int fi = 0; fi < 2 * D; ++fi) {
-            const int k = fi >> 1, side = (fi & 1) ? 1 : -1;
-            int q;
-            if (!in_box(g, l, k, c[k] + side, &q)) continue;
-            int nb[3] = {c[0], c[1], c[2]};
-            nb[k] = q;
-            if (status(g, l, cell_id(g, l, nb[0], nb[1], nb[2])) != 2) continue;
-            const int opp = 2 * k + (side > 0 ? 0 : 1);
-            long long ch[NT];
-            for (int tt = 0; tt < NT; ++tt) {
-                int p[3] = {0, 0, 0}, bit = 0;
-                for (int j = 0; j < D; ++j) {
-                    if (j == k) continue;
-                    p[j] = 2 * nb[j] + ((tt >> bit) & 1);
-                    ++bit;
-                }
-                p[k] = 2 * nb[k] + (side > 0 ? 0 : 1);
-                ch[tt] = cell_id(g, l + 1, p[0], p[1], p[2]);
-                if (status(g, l + 1, ch[tt]) != 1) atomicOr(g.err, ERR_REFLUX);
-            }
-            double* rc = g.rc + g.off[l] * g.nf * m + id;
-            double* rf = g.rf + g.off[l + 1] * g.nf * m;
-            double* qe = fbase_w(g, F_QE, l) + id;
-            const double idx = 1.0 / g.dx[l][k];
-            for (int v = 0; v < m; ++v) {
-                double sum = 0.0;
-                for (int tt = 0; tt < NT; ++tt) {
-                    double* r = rf + (long long)(opp * m + v) * Nf + ch[tt];
-                    sum += *r;
-                    *r = 0.0;
-                }
-                double* r = rc + (long long)(fi * m + v) * N;
-                qe[v * N] += side * (*r - sum * (1.0 / NT)) * idx;
-                *r = 0.0;
-            }
-        }
-    }
-  }
+    dev_reflux<D>(g, lo, hi);
 }
 
 // ------------------------------------------------------------ reductions
-__global__ void k_scale(Grid g, int l)
+__global__ void k_scale(const __grid_constant__ Grid g, int l)
 {
     pdl_enter();
-    const int cnt = g.counts[l];
-    const int* list = g.leaves + g.off[l];
-    const long long N = g.N[l];
-    double mx[MMAX] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    GRID_STRIDE(t, cnt)
-    {
-        const long long id = list[t];
-        if (id < 0 || id >= N) continue;
-        for (int v = 0; v < g.m; ++v) mx[v] = fmax(mx[v], fabs(fbase(g, F_Q0, l)[v * N + id]));
-    }
-    for (int v = 0; v < g.m; ++v) {
-        double a = mx[v];
-        for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-        if ((threadIdx.x & 31) == 0 && a > 0.0)
-            atomicMax(&g.scale_bits[v], (unsigned long long)__double_as_longlong(a));
-    }
+    dev_scale(g, l, l);
 }
 
-__global__ void k_finite(Grid g, int l)
+__global__ void k_finite(const __grid_constant__ Grid g, int l)
 {
     pdl_enter();
-    const int cnt = g.counts[l];
-    const int* list = g.leaves + g.off[l];
-    const long long N = g.N[l];
-    GRID_STRIDE(t, cnt)
-    {
-        const long long id = list[t];
-        if (id < 0 || id >= N) continue;
-        for (int v = 0; v < g.m; ++v)
-            if (!isfinite(fbase(g, F_QE, l)[v * N + id])) atomicOr(g.err, ERR_NONFINITE);
-    }
+    dev_finite(g, l, l);
 }
 
 // fixed-shape partial sums (deterministic): part[block * m + v]
@@ -723,7 +214,7 @@ __global__ void k_uni_down(Grid g, int l, double* T, uint8_t* us)
         const int P[3] = {c[0] >> 1, c[1] >> 1, c[2] >> 1};
         for (int v = 0; v < g.m; ++v) {
             double acc = 0.0;
-            FOR3(D, dx, dy, dz)
+            MRLT_FOR3(D, dx, dy, dz)
             {
                 int neg = 0;
                 const int x = wrap_or_mirror(g, l - 1, 0, P[0] + dx, neg);
@@ -794,7 +285,7 @@ void Launcher::apply_tree(int la) { MRLT_DM_DISPATCH(apply_dm, *this, la); }
 
 void Launcher::compact(int lo, int hi)
 {
-    LevelBlocks lbk;
+    LevelChunks lbk;
     lbk.lo = lo;
     lbk.hi = hi;
     int total = 0;

@@ -1,10 +1,9 @@
 // mrlt_tree.cuh -- host-side launcher of the tree kernels (private).
 #pragma once
-#include "mrlt_impl.cuh"
+#include "mrlt_tree_dev.cuh"
 
 namespace mrlt {
 
-enum ProjMode { PM_Q0 = 0, PM_Q1, PM_Q2, PM_REF2, PM_PRJ2, PM_REF3, PM_PRJ3, PM_MID };
 constexpr int MASS_BLOCKS = 64;
 
 struct Launcher {

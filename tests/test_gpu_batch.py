@@ -45,6 +45,7 @@ def test_batch_equals_standalone_bitwise():
         b.step(t)
     for i, (p, q) in enumerate(zip(probs, qs)):
         s = pkg.Solver(p, q)
+        s.set_launch_mode(pkg.MR_LAUNCH_GRAPH)  # the batch instances' launch path
         s.step(0.02)
         s.step(0.04)
         kb, vb = b.instances[i].leaves()

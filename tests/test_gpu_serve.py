@@ -98,6 +98,7 @@ def test_serve_results_equal_standalone(caps, prec):
         assert srv.status(rid) == 0
         r = srv.result(rid)
         s = pkg.Solver(p, q)
+        s.set_launch_mode(pkg.MR_LAUNCH_GRAPH)  # the served requests' launch path
         s.step(t)
         kr, vr = r.leaves()
         ks, vs = s.leaves()
