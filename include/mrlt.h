@@ -53,10 +53,14 @@ enum { MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_EULER = 2, MR_EQ_REACTION_D
 enum { MR_BC_PERIODIC = 0, MR_BC_NEUMANN = 1, MR_BC_DIRICHLET0 = 2 };
 enum { MR_TIME_GTS = 0, MR_TIME_LT_NERK = 1 };
 enum { MR_ADAPT_NEVER = 0, MR_ADAPT_MACRO = 1, MR_ADAPT_EVERY = 2 };
-/* Arithmetic of the stage kernels.  MR_PREC_MIXED evaluates the MUSCL
- * reconstruction and the numerical face fluxes in FP32; the stored cell
- * averages, the RK updates, the flux registers, the CFL reduction and the whole
- * adaptation (details, thresholds, prediction, projection) stay FP64. */
+/* Precision.  MR_PREC_MIXED stores the cell averages of every node in FP32
+ * and does the stage arithmetic in FP32: exposures and NERK values, MUSCL
+ * reconstruction, numerical fluxes, the compact RK updates and the
+ * projections.  The conservative flux registers accumulate in FP64 (their
+ * correction is rounded to FP32 once), and the detail norms and the
+ * threshold test are evaluated in FP64 from the stored values (as are the
+ * predictions of new nodes and the CFL reduction).  Host-side data
+ * (mr_create, mr_read) stay double in both modes. */
 enum { MR_PREC_FP64 = 0, MR_PREC_MIXED = 1 };
 /* Numerical flux.  MR_FLUX_AUSM_PLUS (Euler only) is the advection upstream
  * splitting of Liou (1996), the flux the paper uses for its Euler cases

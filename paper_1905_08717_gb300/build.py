@@ -17,9 +17,10 @@ LIB = os.path.join(CSRC, "libmrlt.so")
 # equation so that the heaviest translation units build in parallel
 UNITS = [("mrlt_api.cu", [], "api"), ("mrlt_tree.cu", [], "tree"), ("mrlt_stage.cu", [], "stage"),
          ("mrlt_noalloc.cu", [], "noalloc")] + [
-            ("mrlt_stage_eq.cu", [f"-DMRLT_STAGE_EQ={e}"], f"stage_eq{e}") for e in range(4)]
+            ("mrlt_stage_eq.cu", [f"-DMRLT_STAGE_EQ={e}"], f"stage_eq{e}") for e in range(4)] + [
+            ("mrlt_macro_eq.cu", [f"-DMRLT_STAGE_EQ={e}"], f"macro_eq{e}") for e in range(4)]
 SOURCES = sorted({u[0] for u in UNITS})
-HEADERS = ["mrlt_impl.cuh", "mrlt_tree.cuh", "mrlt_stage.cuh"]
+HEADERS = ["mrlt_impl.cuh", "mrlt_tree.cuh", "mrlt_tree_dev.cuh", "mrlt_stage.cuh", "mrlt_macro.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]

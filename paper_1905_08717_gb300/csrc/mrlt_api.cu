@@ -543,7 +543,8 @@ mr_status init_state(mr_solver* h, const double* q0)
     Grid& g = h->K.g;
     const int m = g.m;
     const size_t nd = (size_t)h->ntot * m;
-    for (int f = 0; f < NFIELD; ++f) MR_CK(cudaMemsetAsync(g.f[f], 0, nd * sizeof(double), h->stream));
+    const size_t esz = g.prec ? sizeof(float) : sizeof(double); // field element
+    for (int f = 0; f < NFIELD; ++f) MR_CK(cudaMemsetAsync(g.f[f], 0, nd * esz, h->stream));
     if (g.rc) {
         MR_CK(cudaMemsetAsync(g.rc, 0, nd * g.nf * sizeof(double), h->stream));
         MR_CK(cudaMemsetAsync(g.rf, 0, nd * g.nf * sizeof(double), h->stream));
@@ -553,8 +554,14 @@ mr_status init_state(mr_solver* h, const double* q0)
     MR_CK(cudaMemsetAsync(g.err, 0, sizeof(int), h->stream));
     MR_CK(cudaMemsetAsync(g.near, 0, sizeof(unsigned long long), h->stream));
     MR_CK(cudaMemsetAsync(g.updates, 0, sizeof(unsigned long long), h->stream));
-    MR_CK(cudaMemcpyAsync(g.f[F_Q0] + g.off[g.L] * m, q0, (size_t)g.N[g.L] * m * sizeof(double),
-                          cudaMemcpyHostToDevice, h->stream));
+    if (g.prec) { // FP32 state: through the double scratch, rounded on the device
+        MR_CK(cudaMemcpyAsync(h->d_T, q0, (size_t)g.N[g.L] * m * sizeof(double), cudaMemcpyHostToDevice,
+                              h->stream));
+        h->K.store_finest(h->d_T);
+    } else {
+        MR_CK(cudaMemcpyAsync(static_cast<double*>(g.f[F_Q0]) + g.off[g.L] * m, q0,
+                              (size_t)g.N[g.L] * m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
     for (int l = g.lb; l <= g.L; ++l)
         MR_CK(cudaMemsetAsync(g.st + g.off[l], l < g.L ? 2 : 1, (size_t)g.N[l], h->stream));
     h->K.compact(g.lb, g.L);
@@ -625,7 +632,11 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     };
     A(dev_alloc(h, &g.st, off));
     A(dev_alloc(h, &g.flag, off));
-    for (int f = 0; f < NFIELD; ++f) A(dev_alloc(h, &g.f[f], nd));
+    for (int f = 0; f < NFIELD; ++f) { // double, or float in the mixed mode
+        unsigned char* p = nullptr;
+        A(dev_alloc(h, &p, nd * (g.prec ? sizeof(float) : sizeof(double))));
+        g.f[f] = p;
+    }
     if (h->reg) {
         A(dev_alloc(h, &g.rc, nd * g.nf));
         A(dev_alloc(h, &g.rf, nd * g.nf));

@@ -6,7 +6,9 @@
 //   cell id = i + n_l (j + n_l k), n_l = 2^l.  All levels of one quantity
 //   live in one "pyramid" allocation at offset off[l] (cells).
 //   - status pyramid (uint8): 0 absent, 1 leaf, 2 internal node
-//   - field pyramids (float64, SoA per level: [off_l * m + v * N_l + id]):
+//   - field pyramids (SoA per level: [off_l * m + v * N_l + id]), float64, or
+//     float32 in the mixed-precision mode (the state is stored, and the stage
+//     arithmetic done, in FP32; registers and the detail test stay FP64):
 //       Q0 q^n, Q1 q*, Q2 q**, QE q^{n+1} (leaves: compact RK stages of Sec. 3;
 //       internal nodes: the projections / refreshed values of Algs. 3-9),
 //       XH half-step value (Eq. 17), NH, N1, N3 the NERK theta = 1/2, 1/4, 3/4
@@ -41,7 +43,7 @@ enum ErrBits { ERR_INDEX = 1, ERR_SOURCE = 2, ERR_NONFINITE = 4, ERR_REFLUX = 8,
 struct Grid {
     uint8_t* st;
     uint8_t* flag;
-    double* f[NFIELD];
+    void* f[NFIELD];                // field pyramids: double, or float when prec = 1
     double* rc;
     double* rf;
     int* leaves;
@@ -69,7 +71,7 @@ struct Grid {
     double phys[8];
     double eps;
     int eps_mode;
-    int prec;                       // 0 FP64, 1 mixed: face fluxes in FP32
+    int prec;                       // 0 FP64, 1 mixed: state, fluxes and stage updates in FP32
     int flux;                       // Euler: 0 HLL, 1 AUSM+
     double igm;                     // Euler: 1 / (gamma - 1)
     int gcap;                       // CTAs per stage launch at most (0: resident capacity)
@@ -156,13 +158,11 @@ __device__ __forceinline__ void cell_xyz(const Grid& g, int l, long long id, int
     c[2] = g.d > 2 ? (int)(id >> (2 * l)) : 0;
 }
 
-__device__ __forceinline__ const double* fbase(const Grid& g, int f, int l)
+// level l of field f, stored as T (double, or float in the mixed mode)
+template <class T>
+__device__ __forceinline__ T* fld(const Grid& g, int f, int l)
 {
-    return g.f[f] + g.off[l] * g.m;
-}
-__device__ __forceinline__ double* fbase_w(const Grid& g, int f, int l)
-{
-    return g.f[f] + g.off[l] * g.m;
+    return static_cast<T*>(g.f[f]) + g.off[l] * g.m;
 }
 
 __device__ __forceinline__ uint8_t status(const Grid& g, int l, long long id)
@@ -176,97 +176,98 @@ __device__ __forceinline__ uint8_t status(const Grid& g, int l, long long id)
 // stage values: with k1 = q* - q^n and k2 the second stage increment
 // (RK2: k2 = 2 q^{n+1} - q^n - q*, RK3: k2 = 4 q** - 3 q^n - q*),
 // q(theta) = q^n + (theta - theta^2/2) k1 + theta^2/2 k2 (Sec. 3 NERK2).
-template <int M>
-__device__ __forceinline__ void expose(const Grid& g, const Ctx& x, int l, long long id, int st,
-                                       double* out)
+// T is the storage type of the fields, O the arithmetic type of the result.
+template <int M, class T, class O>
+__device__ __forceinline__ void expose(const Grid& g, const Ctx& x, int l, long long id, int st, O* out)
 {
     const long long N = g.N[l];
-    const double* q0 = fbase(g, F_Q0, l) + id;
-    const double* q1 = fbase(g, F_Q1, l) + id;
-    const double* q2 = fbase(g, F_Q2, l) + id;
-    const double* qe = fbase(g, F_QE, l) + id;
+    const T* q0 = fld<T>(g, F_Q0, l) + id;
+    const T* q1 = fld<T>(g, F_Q1, l) + id;
+    const T* q2 = fld<T>(g, F_Q2, l) + id;
+    const T* qe = fld<T>(g, F_QE, l) + id;
     const int s = x.s;
     const int rel = l - x.u;
     if (s == 0 || (s == 1 && g.gts) || (s == 1 && (rel >= 0 || l >= x.lmin))) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = q0[v * N];
+        for (int v = 0; v < M; ++v) out[v] = O(q0[v * N]);
         return;
     }
     if (g.gts) {
-        const double* a = s == 2 ? q1 : q2;
+        const T* a = s == 2 ? q1 : q2;
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = a[v * N];
+        for (int v = 0; v < M; ++v) out[v] = O(a[v * N]);
         return;
     }
     if (s == 1) { // coarser level lmin-1, mid-step: theta = 1/2 value
         if (g.rk == 3) {
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = q2[v * N];
+            for (int v = 0; v < M; ++v) out[v] = O(q2[v * N]);
         } else if (st == 1) {
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = 0.5 * q0[v * N] + 0.25 * q1[v * N] + 0.25 * qe[v * N];
+            for (int v = 0; v < M; ++v)
+                out[v] = O(0.5) * O(q0[v * N]) + O(0.25) * O(q1[v * N]) + O(0.25) * O(qe[v * N]);
         } else {
-            const double* nh = fbase(g, F_NH, l) + id;
+            const T* nh = fld<T>(g, F_NH, l) + id;
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = nh[v * N];
+            for (int v = 0; v < M; ++v) out[v] = O(nh[v * N]);
         }
         return;
     }
     if (s == 2) {
         if (rel == 0) {
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = q1[v * N];
+            for (int v = 0; v < M; ++v) out[v] = O(q1[v * N]);
         } else if (rel == 1) {
             if (st == 1) { // Eq. 14: q* + k2
                 if (g.rk == 2) {
 #pragma unroll
-                    for (int v = 0; v < M; ++v) out[v] = 2.0 * qe[v * N] - q0[v * N];
+                    for (int v = 0; v < M; ++v) out[v] = O(2) * O(qe[v * N]) - O(q0[v * N]);
                 } else {
 #pragma unroll
-                    for (int v = 0; v < M; ++v) out[v] = 4.0 * q2[v * N] - 3.0 * q0[v * N];
+                    for (int v = 0; v < M; ++v) out[v] = O(4) * O(q2[v * N]) - O(3) * O(q0[v * N]);
                 }
             } else { // Eq. 15
 #pragma unroll
-                for (int v = 0; v < M; ++v) out[v] = 2.0 * q1[v * N] - q0[v * N];
+                for (int v = 0; v < M; ++v) out[v] = O(2) * O(q1[v * N]) - O(q0[v * N]);
             }
         } else if (l >= x.lmin) { // half step of the coarser level
             if (st == 1) {
 #pragma unroll
-                for (int v = 0; v < M; ++v) out[v] = q0[v * N] + 0.5 * (q1[v * N] - q0[v * N]);
+                for (int v = 0; v < M; ++v) out[v] = O(q0[v * N]) + O(0.5) * (O(q1[v * N]) - O(q0[v * N]));
             } else {
-                const double* xh = fbase(g, F_XH, l) + id;
+                const T* xh = fld<T>(g, F_XH, l) + id;
 #pragma unroll
-                for (int v = 0; v < M; ++v) out[v] = xh[v * N];
+                for (int v = 0; v < M; ++v) out[v] = O(xh[v * N]);
             }
         } else { // end of the mid-step coarser level
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = qe[v * N];
+            for (int v = 0; v < M; ++v) out[v] = O(qe[v * N]);
         }
         return;
     }
     // stage 3
     if (rel == 0) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = q2[v * N];
+        for (int v = 0; v < M; ++v) out[v] = O(q2[v * N]);
     } else if (rel == 1) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = qe[v * N];
+        for (int v = 0; v < M; ++v) out[v] = O(qe[v * N]);
     } else {
         const bool act = l >= x.lmin;
         if (st == 1) {
-            const double b1 = act ? 7.0 / 32.0 : 15.0 / 32.0;
-            const double b2 = act ? 1.0 / 32.0 : 9.0 / 32.0;
+            const O b1 = act ? O(7.0 / 32.0) : O(15.0 / 32.0);
+            const O b2 = act ? O(1.0 / 32.0) : O(9.0 / 32.0);
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                const double a0 = q0[v * N], a1 = q1[v * N];
-                const double k1 = a1 - a0;
-                const double k2 = 4.0 * q2[v * N] - 3.0 * a0 - a1;
+                const O a0 = O(q0[v * N]), a1 = O(q1[v * N]);
+                const O k1 = a1 - a0;
+                const O k2 = O(4) * O(q2[v * N]) - O(3) * a0 - a1;
                 out[v] = a0 + b1 * k1 + b2 * k2;
             }
         } else {
-            const double* nn = fbase(g, act ? F_N1 : F_N3, l) + id;
+            const T* nn = fld<T>(g, act ? F_N1 : F_N3, l) + id;
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = nn[v * N];
+            for (int v = 0; v < M; ++v) out[v] = O(nn[v * N]);
         }
     }
 }
@@ -283,12 +284,12 @@ __device__ __forceinline__ double pw(int a, int delta)
 // Tensor-product prediction (Eq. 4 applied along each direction) of the cell
 // at in-box coordinates q of level l from the 3^d stored nodes of level l-1
 // around its parent, using their exposures.
-template <int D, int M>
-__device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, const int q[3], double* out)
+template <int D, int M, class T, class O>
+__device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, const int q[3], O* out)
 {
     const int pl = l - 1;
 #pragma unroll
-    for (int v = 0; v < M; ++v) out[v] = 0.0;
+    for (int v = 0; v < M; ++v) out[v] = O(0);
     if (pl < g.lb) {
         atomicOr(g.err, ERR_SOURCE);
         return;
@@ -301,12 +302,12 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
     for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
         int nz = 0;
         const int z = D > 2 ? wrap_or_mirror(g, pl, 2, P2 + dz, nz) : 0;
-        const double wz = D > 2 ? pw(a2, dz) : 1.0;
+        const O wz = D > 2 ? O(pw(a2, dz)) : O(1);
 #pragma unroll(D > 2 ? 1 : 3)
         for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
             int nyz = nz;
             const int y = D > 1 ? wrap_or_mirror(g, pl, 1, P1 + dy, nyz) : 0;
-            const double wyz = wz * (D > 1 ? pw(a1, dy) : 1.0);
+            const O wyz = wz * (D > 1 ? O(pw(a1, dy)) : O(1));
 #pragma unroll
             for (int dxx = -1; dxx <= 1; ++dxx) {
                 int neg = nyz;
@@ -317,10 +318,10 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
                     atomicOr(g.err, ERR_SOURCE);
                     continue;
                 }
-                double val[M];
-                expose<M>(g, x, pl, id, st, val);
-                const double w0 = wyz * pw(a0, dxx);
-                const double w = neg ? -w0 : w0; // an odd-mirror ghost enters negated
+                O val[M];
+                expose<M, T, O>(g, x, pl, id, st, val);
+                const O w0 = wyz * O(pw(a0, dxx));
+                const O w = neg ? -w0 : w0; // an odd-mirror ghost enters negated
 #pragma unroll
                 for (int v = 0; v < M; ++v) out[v] += w * val[v];
             }
@@ -333,7 +334,7 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
 // once and enters every child with that child's weights.  Each child's sum
 // runs over the block in the order of predict(), so out[k] equals
 // predict(g, x, l + 1, 2 c + k) term by term.
-template <int D, int M>
+template <int D, int M, class T>
 __device__ __forceinline__ void predict_children(const Grid& g, const Ctx& x, int l, const int c[3],
                                                  double (*out)[M])
 {
@@ -361,7 +362,7 @@ __device__ __forceinline__ void predict_children(const Grid& g, const Ctx& x, in
                     continue;
                 }
                 double val[M];
-                expose<M>(g, x, l, id, st, val);
+                expose<M, T, double>(g, x, l, id, st, val);
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {
                     const double wz = D > 2 ? pw((k >> 2) & 1, dz) : 1.0;
@@ -377,8 +378,8 @@ __device__ __forceinline__ void predict_children(const Grid& g, const Ctx& x, in
 }
 
 // value of the cell at (possibly out-of-box) coordinates p on level l
-template <int D, int M>
-__device__ __forceinline__ void value_at(const Grid& g, const Ctx& x, int l, const int p[3], double* out)
+template <int D, int M, class T, class O>
+__device__ __forceinline__ void value_at(const Grid& g, const Ctx& x, int l, const int p[3], O* out)
 {
     int q[3] = {0, 0, 0};
     int neg = 0;
@@ -386,8 +387,8 @@ __device__ __forceinline__ void value_at(const Grid& g, const Ctx& x, int l, con
     for (int k = 0; k < D; ++k) q[k] = wrap_or_mirror(g, l, k, p[k], neg);
     const long long id = cell_id(g, l, q[0], q[1], q[2]);
     const int st = status(g, l, id);
-    if (st) expose<M>(g, x, l, id, st, out);
-    else predict<D, M>(g, x, l, q, out);
+    if (st) expose<M, T, O>(g, x, l, id, st, out);
+    else predict<D, M, T, O>(g, x, l, q, out);
     if (neg) {
 #pragma unroll
         for (int v = 0; v < M; ++v) out[v] = -out[v];
@@ -404,10 +405,10 @@ __device__ __forceinline__ R minmod(R a, R b)
 
 // Variables that MUSCL reconstructs: primitives (rho, u_1..u_d, p) for Euler,
 // the conserved variable itself otherwise.  R is the arithmetic type of the
-// flux evaluation: double, or float in the mixed-precision mode (the stored
-// state W stays double in both).
-template <int EQ, int D, int M, class R>
-__device__ __forceinline__ void recon_vars(const Grid& g, const double* W, R* P)
+// flux evaluation: double, or float in the mixed-precision mode; W holds the
+// conservative values (type WT).
+template <int EQ, int D, int M, class R, class WT>
+__device__ __forceinline__ void recon_vars(const Grid& g, const WT* W, R* P)
 {
     if constexpr (EQ == 2) {
         const R gam = R(g.phys[0]);
@@ -549,14 +550,14 @@ __device__ __forceinline__ void flux_recon(const Grid& g, int k, double dxf, con
     }
 }
 
-template <int EQ, int M>
-__device__ __forceinline__ void source(const Grid& g, const double* q, double* S)
+template <int EQ, int M, class R>
+__device__ __forceinline__ void source(const Grid& g, const R* q, R* S)
 {
 #pragma unroll
-    for (int v = 0; v < M; ++v) S[v] = 0.0;
+    for (int v = 0; v < M; ++v) S[v] = R(0);
     if constexpr (EQ == 3) {
-        const double u = q[0];
-        S[0] = g.phys[1] * u * (1.0 - u) * (u - g.phys[2]);
+        const R u = q[0];
+        S[0] = R(g.phys[1]) * u * (R(1) - u) * (u - R(g.phys[2]));
     }
 }
 

@@ -24,7 +24,8 @@
 namespace mrlt {
 
 
-// Arguments of one macro-step kernel launch.
+// Arguments of one macro-step kernel launch.  (The fields are stored in the
+// stage arithmetic type R: double, or float in the mixed-precision mode.)
 struct MacroArgs {
     long long n0, n1;             // fine iterations [n0, n1) of the macro step
     long long nit;                // fine iterations per macro step, 2^{L - min level}
@@ -109,6 +110,57 @@ __device__ __forceinline__ double rk_weight(const Grid& g, int s)
     return s == 3 ? 2.0 / 3.0 : 1.0 / 6.0;
 }
 
+// Out-of-line phases of the macro-step kernel: each body is compiled once per
+// instantiation however many call sites the iteration has (compile time and
+// code size), at the cost of one call per phase.
+template <int EQ, int D, class R>
+__device__ __noinline__ void mph_stage(const Grid& g, int lo, int hi, int s, int lmin, double b, int reg,
+                                       unsigned char* smem)
+{
+    stage_tiles<EQ, D, R>(g, lo, hi, s, lmin, b, reg, smem);
+}
+template <int D, class T>
+__device__ __noinline__ void mph_project(const Grid& g, int l, int mode)
+{
+    dev_project<D, T>(g, l, mode);
+}
+template <int D, int M, class T>
+__device__ __noinline__ void mph_detail(const Grid& g, int lo, int hi)
+{
+    dev_detail<D, M, T>(g, lo, hi);
+}
+template <int D>
+__device__ __noinline__ void mph_desire(const Grid& g, int lo, int hi, int la)
+{
+    dev_desire<D>(g, lo, hi, la);
+}
+template <int D>
+__device__ __noinline__ void mph_allow(const Grid& g, int lo, int hi, int la)
+{
+    dev_allow<D>(g, lo, hi, la);
+}
+template <int D>
+__device__ __noinline__ void mph_close(const Grid& g, int l)
+{
+    dev_close<D>(g, l);
+}
+template <int D, int M, class T>
+__device__ __noinline__ void mph_apply(const Grid& g, int l, int la)
+{
+    dev_apply<D, M, T>(g, l, la);
+}
+template <int D, class T>
+__device__ __noinline__ void mph_reflux(const Grid& g, int lo, int hi)
+{
+    dev_reflux<D, T>(g, lo, hi);
+}
+template <int EQ, int D, class T>
+__device__ __noinline__ void mph_end(const Grid& g, int lo, int hi)
+{
+    dev_finite<T>(g, lo, hi);
+    dev_wave<EQ, D, T>(g, lo, hi);
+}
+
 template <int EQ, int D, class R>
 __global__ void __launch_bounds__(Tile<D>::THREADS)
 k_macro(const __grid_constant__ Grid g, MacroArgs a)
@@ -144,36 +196,36 @@ k_macro(const __grid_constant__ Grid g, MacroArgs a)
         phase(PH_TREE, L);
         if (adapt_now && lmin == lb && lead)
             for (int v = 0; v < MMAX; ++v) g.scale_bits[v] = (unsigned long long)__double_as_longlong(1e-14);
-        dev_leaf_copy(g, lmin, L, F_QE, F_Q0);
+        dev_leaf_copy<R>(g, lmin, L, F_QE, F_Q0);
         MRLT_SYNC();
         for (int l = L - 1; l >= lmin; --l) {
             phase(PH_TREE, l);
-            dev_project<D>(g, l, PM_Q0);
+            mph_project<D, R>(g, l, PM_Q0);
             MRLT_SYNC();
         }
         if (adapt_now) { // restricted remesh of levels >= la = lmin (Sec. 4)
             const int la = lmin;
             phase(PH_ADAPT, 0);
-            if (la == lb) dev_scale(g, lb, L);
+            if (la == lb) dev_scale<R>(g, lb, L);
             dev_clear_flags(g, g.off[la], g.off[L] + g.N[L]);
             MRLT_SYNC();
             phase(PH_ADAPT, 1);
-            dev_detail<D, M>(g, la, L - 1);
+            mph_detail<D, M, R>(g, la, L - 1);
             MRLT_SYNC();
             phase(PH_ADAPT, 2);
-            dev_desire<D>(g, la, L - 1, la);
+            mph_desire<D>(g, la, L - 1, la);
             MRLT_SYNC();
             phase(PH_ADAPT, 3);
-            dev_allow<D>(g, la, L - 1, la);
+            mph_allow<D>(g, la, L - 1, la);
             MRLT_SYNC();
             for (int l = L - 1; l > la; --l) {
                 phase(PH_ADAPT, 4);
-                dev_close<D>(g, l);
+                mph_close<D>(g, l);
                 MRLT_SYNC();
             }
             for (int l = la; l <= L; ++l) {
                 phase(PH_ADAPT, 5);
-                dev_apply<D, M>(g, l, la);
+                mph_apply<D, M, R>(g, l, la);
                 MRLT_SYNC();
             }
             // leaf, node and active-tile lists of levels la..L (chunks of NT cells)
@@ -204,7 +256,7 @@ k_macro(const __grid_constant__ Grid g, MacroArgs a)
             MRLT_SYNC();
             for (int l = L - 1; l >= la; --l) {
                 phase(PH_ADAPT, 10);
-                dev_project<D>(g, l, PM_Q0);
+                mph_project<D, R>(g, l, PM_Q0);
                 MRLT_SYNC();
             }
         }
@@ -213,53 +265,53 @@ k_macro(const __grid_constant__ Grid g, MacroArgs a)
                 if (s > 1)
                     for (int l = L - 1; l >= lb; --l) {
                         phase(PH_TREE, l);
-                        dev_project<D>(g, l, s == 2 ? PM_Q1 : PM_Q2);
+                        mph_project<D, R>(g, l, s == 2 ? PM_Q1 : PM_Q2);
                         MRLT_SYNC();
                     }
                 phase(PH_STAGE1 + s - 1, L);
-                stage_tiles<EQ, D, R>(g, lb, L, s, lb, rk_weight(g, s), 0, smem);
+                mph_stage<EQ, D, R>(g, lb, L, s, lb, rk_weight(g, s), 0, smem);
                 MRLT_SYNC();
             }
             continue;
         }
         if (lmin > lb) { // Alg. 3 / Sec. 4.3: the mid-step level lmin - 1
             phase(PH_TREE, lmin - 1);
-            dev_project<D>(g, lmin - 1, PM_MID);
+            mph_project<D, R>(g, lmin - 1, PM_MID);
             MRLT_SYNC();
         }
         // first RK stage on every active level (independent levels: one phase)
         phase(PH_STAGE1, L);
-        stage_tiles<EQ, D, R>(g, lmin, L, 1, lmin, rk_weight(g, 1), a.reg, smem);
+        mph_stage<EQ, D, R>(g, lmin, L, 1, lmin, rk_weight(g, 1), a.reg, smem);
         MRLT_SYNC();
         for (int l = L - 1; l >= lmin; --l) { // Alg. 8
             phase(PH_TREE, l);
-            dev_project<D>(g, l, PM_REF2);
+            mph_project<D, R>(g, l, PM_REF2);
             MRLT_SYNC();
         }
         for (int l = L; l >= lmin; --l) { // Alg. 5 with the Alg. 4 projections
             if (l < L) {
                 phase(PH_TREE, l);
-                dev_project<D>(g, l, PM_PRJ2);
+                mph_project<D, R>(g, l, PM_PRJ2);
                 MRLT_SYNC();
             }
             phase(PH_STAGE2, l);
-            stage_tiles<EQ, D, R>(g, l, l, 2, lmin, rk_weight(g, 2), a.reg, smem);
+            mph_stage<EQ, D, R>(g, l, l, 2, lmin, rk_weight(g, 2), a.reg, smem);
             MRLT_SYNC();
         }
         if (g.rk == 3) {
             for (int l = L - 1; l >= lmin; --l) { // Alg. 9
                 phase(PH_TREE, l);
-                dev_project<D>(g, l, PM_REF3);
+                mph_project<D, R>(g, l, PM_REF3);
                 MRLT_SYNC();
             }
             for (int l = L; l >= lmin; --l) { // Alg. 7 with the Alg. 6 projections
                 if (l < L) {
                     phase(PH_TREE, l);
-                    dev_project<D>(g, l, PM_PRJ3);
+                    mph_project<D, R>(g, l, PM_PRJ3);
                     MRLT_SYNC();
                 }
                 phase(PH_STAGE3, l);
-                stage_tiles<EQ, D, R>(g, l, l, 3, lmin, rk_weight(g, 3), a.reg, smem);
+                mph_stage<EQ, D, R>(g, l, l, 3, lmin, rk_weight(g, 3), a.reg, smem);
                 MRLT_SYNC();
             }
         }
@@ -267,15 +319,14 @@ k_macro(const __grid_constant__ Grid g, MacroArgs a)
             const int lc = (n + 1 == a.nit) ? lb : level_min_dev(g, n + 1);
             if (lc < L) {
                 phase(PH_TREE, lc);
-                dev_reflux<D>(g, lc, L - 1);
+                mph_reflux<D, R>(g, lc, L - 1);
                 MRLT_SYNC();
             }
         }
     }
     if (a.end_of_macro) { // after the macro step: finiteness check and CFL wave speed
         phase(PH_TREE, lb);
-        dev_finite(g, lb, L);
-        dev_wave<EQ, D>(g, lb, L);
+        mph_end<EQ, D, R>(g, lb, L);
     }
     phase(PH_END, 0);
 #undef MRLT_SYNC

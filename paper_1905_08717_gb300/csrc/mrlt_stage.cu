@@ -6,11 +6,11 @@
 namespace mrlt {
 
 // largest sum of characteristic speeds over the leaves of level l (CFL step)
-template <int EQ, int D>
+template <int EQ, int D, class T>
 __global__ void __launch_bounds__(NTHREADS) k_wave(const __grid_constant__ Grid g, int l)
 {
     pdl_enter();
-    dev_wave<EQ, D>(g, l, l);
+    dev_wave<EQ, D, T>(g, l, l);
 }
 
 int launch_stage(const Grid& g, cudaStream_t st, int lo, int hi, int s, int lmin, double b, int reg)
@@ -53,10 +53,11 @@ int launch_grid_wait_test(cudaStream_t st, int ctas, int missing, unsigned long 
 
 void launch_wave(const Grid& g, cudaStream_t st, int l)
 {
-#define MRLT_CASE(E, DD)                                          \
-    if (g.eq == E && g.d == DD) {                                 \
-        k_wave<E, DD><<<grid_for(g, l), NTHREADS, 0, st>>>(g, l); \
-        return;                                                   \
+#define MRLT_CASE(E, DD)                                                                         \
+    if (g.eq == E && g.d == DD) {                                                                \
+        if (g.prec) k_wave<E, DD, float><<<grid_for(g, l), NTHREADS, 0, st>>>(g, l);            \
+        else k_wave<E, DD, double><<<grid_for(g, l), NTHREADS, 0, st>>>(g, l);                  \
+        return;                                                                                  \
     }
     MRLT_CASE(0, 1) MRLT_CASE(0, 2) MRLT_CASE(0, 3)
     MRLT_CASE(1, 1) MRLT_CASE(1, 2) MRLT_CASE(1, 3)

@@ -4,8 +4,9 @@
 // k_stage_tile (d = 1, 2, 3) works on one tile of one level per CTA: the
 // halo is staged in shared memory and every face flux is computed once.  It is
 // instantiated for R = double and, for the mixed-precision mode, R = float:
-// reconstruction and numerical flux in R; the stored state, the right-hand
-// side, the RK update and the flux registers stay in double.
+// the stored state, the exposures, the reconstruction, the numerical fluxes,
+// the right-hand side and the RK update are all in R; the flux registers
+// accumulate in double.
 #pragma once
 #include "mrlt_impl.cuh"
 
@@ -17,24 +18,24 @@ namespace mrlt {
 //   s = 3: q^{n+1} = q^n/3 + 2q**/3 + 2 dt_l f/3
 // qs is the leaf's own value at stage s (q^n, q*, q** for s = 1, 2, 3: its
 // exposure, already staged in shared memory) and q0 its q^n (s >= 2).
-template <int M>
-__device__ __forceinline__ void rk_update(const Grid& g, int u, long long id, int s, double dtl, const double* f,
-                                          const double* q0, const double* qs)
+template <int M, class R>
+__device__ __forceinline__ void rk_update(const Grid& g, int u, long long id, int s, R dtl, const R* f, const R* q0,
+                                          const R* qs)
 {
     const long long N = g.N[u];
-    double* q1 = fbase_w(g, F_Q1, u) + id;
-    double* q2 = fbase_w(g, F_Q2, u) + id;
-    double* qe = fbase_w(g, F_QE, u) + id;
+    R* q1 = fld<R>(g, F_Q1, u) + id;
+    R* q2 = fld<R>(g, F_Q2, u) + id;
+    R* qe = fld<R>(g, F_QE, u) + id;
 #pragma unroll
     for (int v = 0; v < M; ++v) {
-        const double kk = dtl * f[v];
+        const R kk = dtl * f[v];
         if (s == 1) {
             q1[v * N] = qs[v] + kk;
         } else if (s == 2) {
-            if (g.rk == 2) qe[v * N] = 0.5 * q0[v] + 0.5 * qs[v] + 0.5 * kk;
-            else q2[v * N] = 0.75 * q0[v] + 0.25 * qs[v] + 0.25 * kk;
+            if (g.rk == 2) qe[v * N] = R(0.5) * q0[v] + R(0.5) * qs[v] + R(0.5) * kk;
+            else q2[v * N] = R(0.75) * q0[v] + R(0.25) * qs[v] + R(0.25) * kk;
         } else {
-            qe[v * N] = (1.0 / 3.0) * q0[v] + (2.0 / 3.0) * qs[v] + (2.0 / 3.0) * kk;
+            qe[v * N] = R(1.0 / 3.0) * q0[v] + R(2.0 / 3.0) * qs[v] + R(2.0 / 3.0) * kk;
         }
     }
 }
@@ -81,11 +82,10 @@ struct TileShape {
     static constexpr int PB = PBX * PBY * PBZ;
     // sub-face tasks whose two finer-side cells are fetched with the exposures
     static constexpr int NPF = D > 2 ? 64 : NT;
-    // dynamic shared memory: conservative values of the block, of the parent
-    // block and q^n of the tile (double), reconstruction variables, face
-    // fluxes and the prefetched finer-side variables (R)
-    static constexpr size_t SMEM = sizeof(double) * M * (NB + PB + NC) +
-                                   sizeof(R) * M * (NB + NF + 2 * NPF);
+    // dynamic shared memory (all R): conservative values of the block, of the
+    // parent block and q^n of the tile, reconstruction variables, face fluxes
+    // and the prefetched finer-side variables
+    static constexpr size_t SMEM = sizeof(R) * M * (2 * NB + PB + NC + NF + 2 * NPF);
 };
 
 // Append, in thread order, `item` to list A where `ta` holds and to list B
@@ -130,15 +130,15 @@ __device__ __forceinline__ void block_append2(bool ta, bool tb, int item, short*
 // expose()), with its status and every field the choice may need loaded at
 // once: one memory round trip instead of status, then fields.  Returns false
 // (out untouched) when the cell is absent.
-template <int M>
-__device__ __forceinline__ bool finer_exposure(const Grid& g, const Ctx& x, int l, const int q[3], double* out)
+template <int M, class T>
+__device__ __forceinline__ bool finer_exposure(const Grid& g, const Ctx& x, int l, const int q[3], T* out)
 {
     const long long id = cell_id(g, l, q[0], q[1], q[2]);
     const long long N = g.N[l];
-    const double* q0 = fbase(g, F_Q0, l) + id;
+    const T* q0 = fld<T>(g, F_Q0, l) + id;
     const int st = status(g, l, id);
     if (x.s <= 1) {
-        double a[M];
+        T a[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) a[v] = q0[v * N];
         if (st == 0) return false;
@@ -147,8 +147,8 @@ __device__ __forceinline__ bool finer_exposure(const Grid& g, const Ctx& x, int 
         return true;
     }
     if (g.gts || x.s == 3) { // global step: q* / q**; LT stage 3: q^{n+1} of the first sub-step
-        const double* a = fbase(g, g.gts ? (x.s == 2 ? F_Q1 : F_Q2) : F_QE, l) + id;
-        double b[M];
+        const T* a = fld<T>(g, g.gts ? (x.s == 2 ? F_Q1 : F_Q2) : F_QE, l) + id;
+        T b[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) b[v] = a[v * N];
         if (st == 0) return false;
@@ -157,9 +157,9 @@ __device__ __forceinline__ bool finer_exposure(const Grid& g, const Ctx& x, int 
         return true;
     }
     // LT stage 2: leaf Eq. 14 (q* + k2), internal node Eq. 15 (2 q* - q^n)
-    const double* q1 = fbase(g, F_Q1, l) + id;
-    const double* qx = fbase(g, g.rk == 2 ? F_QE : F_Q2, l) + id;
-    double a0[M], a1[M], ax[M];
+    const T* q1 = fld<T>(g, F_Q1, l) + id;
+    const T* qx = fld<T>(g, g.rk == 2 ? F_QE : F_Q2, l) + id;
+    T a0[M], a1[M], ax[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) {
         a0[v] = q0[v * N];
@@ -170,14 +170,14 @@ __device__ __forceinline__ bool finer_exposure(const Grid& g, const Ctx& x, int 
     if (st == 1) {
         if (g.rk == 2) {
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = 2.0 * ax[v] - a0[v];
+            for (int v = 0; v < M; ++v) out[v] = T(2) * ax[v] - a0[v];
         } else {
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = 4.0 * ax[v] - 3.0 * a0[v];
+            for (int v = 0; v < M; ++v) out[v] = T(4) * ax[v] - T(3) * a0[v];
         }
     } else {
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = 2.0 * a1[v] - a0[v];
+        for (int v = 0; v < M; ++v) out[v] = T(2) * a1[v] - a0[v];
     }
     return true;
 }
@@ -224,10 +224,10 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
     constexpr int OUT = 3;            // status code of a cell past a wall
     constexpr int SY = BX, SZ = BX * BY;     // block strides in y and z
     constexpr int PSY = PBX, PSZ = PBX * PBY; // parent-block strides
-    double (*sW)[NB] = reinterpret_cast<double (*)[NB]>(smem);
-    double (*sPW)[PB] = reinterpret_cast<double (*)[PB]>(smem + sizeof(double) * M * NB);
-    double (*sQ0)[NC] = reinterpret_cast<double (*)[NC]>(smem + sizeof(double) * M * (NB + PB));
-    unsigned char* rbase = smem + sizeof(double) * M * (NB + PB + NC);
+    R (*sW)[NB] = reinterpret_cast<R (*)[NB]>(smem);
+    R (*sPW)[PB] = reinterpret_cast<R (*)[PB]>(smem + sizeof(R) * M * NB);
+    R (*sQ0)[NC] = reinterpret_cast<R (*)[NC]>(smem + sizeof(R) * M * (NB + PB));
+    unsigned char* rbase = smem + sizeof(R) * M * (NB + PB + NC);
     R (*sP)[NB] = reinterpret_cast<R (*)[NB]>(rbase);
     // x faces [0, NFX), y faces [NFX, NFX + NFY), z faces [NFX + NFY, NF)
     R (*sF)[NF] = reinterpret_cast<R (*)[NF]>(rbase + sizeof(R) * M * NB);
@@ -440,18 +440,18 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
 
     // 3. one trip: exposures of stored and parent cells, finer-side cells of
     //    the first sub-face tasks, q^n of the tile's leaves
-    double q0r[M];
+    R q0r[M];
     const bool own_leaf = s >= 2 && tid < NC &&
                           tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0);
     if (own_leaf) {
         const long long N = g.N[u];
-        const double* q0 = fbase(g, F_Q0, u) + cell_id(g, u, ox + tid % TX, D > 1 ? oy + (tid / TX) % TY : 0,
-                                                       D > 2 ? oz + tid / (TX * TY) : 0);
+        const R* q0 = fld<R>(g, F_Q0, u) + cell_id(g, u, ox + tid % TX, D > 1 ? oy + (tid / TX) % TY : 0,
+                                                   D > 2 ? oz + tid / (TX * TY) : 0);
 #pragma unroll
         for (int v = 0; v < M; ++v) q0r[v] = q0[v * N];
     }
     for (int t = tid; t < nst + npl; t += NT) {
-        double W[M];
+        R W[M];
         if (t < nst) {
             const int b = sList[t];
             const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
@@ -459,7 +459,7 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
             in_box(g, u, 0, ox + bx - H, &qx);
             if (D > 1) in_box(g, u, 1, oy + by - H, &qy);
             if (D > 2) in_box(g, u, 2, oz + bz - H, &qz);
-            expose<M>(g, x, u, cell_id(g, u, qx, qy, qz), sSt[b], W);
+            expose<M, R, R>(g, x, u, cell_id(g, u, qx, qy, qz), sSt[b], W);
             R P[M];
             recon_vars<EQ, D, M, R>(g, W, P);
 #pragma unroll
@@ -476,7 +476,7 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
             const int px = wrap_or_mirror(g, u - 1, 0, pox + i, neg);
             const int py = D > 1 ? wrap_or_mirror(g, u - 1, 1, poy + j, neg) : 0;
             const int pz = D > 2 ? wrap_or_mirror(g, u - 1, 2, poz + kk, neg) : 0;
-            expose<M>(g, x, u - 1, cell_id(g, u - 1, px, py, pz), st, W);
+            expose<M, R, R>(g, x, u - 1, cell_id(g, u - 1, px, py, pz), st, W);
             // an odd-mirror ghost enters negated: (-w) v = w (-v) exactly
 #pragma unroll
             for (int v = 0; v < M; ++v) sPW[v][pb] = neg ? -W[v] : W[v];
@@ -502,9 +502,9 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
             int q[3] = {0, 0, 0}, neg = 0;
 #pragma unroll
             for (int kk = 0; kk < D; ++kk) q[kk] = wrap_or_mirror(g, u + 1, kk, p[kk], neg);
-            double W[M];
-            if (!finer_exposure<M>(g, x, u + 1, q, W)) {
-                value_at<D, M>(g, x, u + 1, p, W); // absent: predicted (flags the missing source)
+            R W[M];
+            if (!finer_exposure<M, R>(g, x, u + 1, q, W)) {
+                value_at<D, M, R, R>(g, x, u + 1, p, W); // absent: predicted (flags the missing source)
             } else if (neg) {
 #pragma unroll
                 for (int v = 0; v < M; ++v) W[v] = -W[v];
@@ -526,17 +526,17 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
         const int b = sList2[t];
         int p[3], q[3], neg, bq, pb0;
         resolve(b, p, q, neg, bq, pb0);
-        double W[M];
+        R W[M];
         if (bq >= 0 && sSt[bq] == 0 && pb0 >= 0) {
 #pragma unroll
-            for (int v = 0; v < M; ++v) W[v] = 0.0;
+            for (int v = 0; v < M; ++v) W[v] = R(0);
             const int a0 = q[0] & 1, a1 = q[1] & 1, a2 = q[2] & 1;
 #pragma unroll(D > 2 ? 1 : 3)
             for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
-                const double wz = D > 2 ? pw(a2, dz) : 1.0;
+                const R wz = D > 2 ? R(pw(a2, dz)) : R(1);
 #pragma unroll(D > 2 ? 1 : 3)
                 for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy) {
-                    const double wyz = wz * (D > 1 ? pw(a1, dy) : 1.0);
+                    const R wyz = wz * (D > 1 ? R(pw(a1, dy)) : R(1));
 #pragma unroll
                     for (int dxx = -1; dxx <= 1; ++dxx) {
                         const int pb = pb0 + (D > 2 ? (dz + 1) * PSZ : 0) + (D > 1 ? (dy + 1) * PSY : 0) + dxx + 1;
@@ -544,7 +544,7 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
                             atomicOr(g.err, ERR_SOURCE);
                             continue;
                         }
-                        const double w0 = wyz * pw(a0, dxx);
+                        const R w0 = wyz * R(pw(a0, dxx));
 #pragma unroll
                         for (int v = 0; v < M; ++v) W[v] += w0 * sPW[v][pb];
                     }
@@ -558,7 +558,7 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
 #pragma unroll
             for (int v = 0; v < M; ++v) W[v] = neg ? -sW[v][bq] : sW[v][bq];
         } else {
-            value_at<D, M>(g, x, u, p, W);
+            value_at<D, M, R, R>(g, x, u, p, W);
         }
         R P[M];
         recon_vars<EQ, D, M, R>(g, W, P);
@@ -608,18 +608,18 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
                     if (D > 2) p[j2] = 2 * c[j2] + (t >> 1);
                     const bool own = side > 0 ? i < 2 : i >= 2;
                     if (own) {
-                        double W[M];
+                        R W[M];
                         const int ax = p[0] & 1, ay = p[1] & 1, az = p[2] & 1;
 #pragma unroll
-                        for (int v = 0; v < M; ++v) W[v] = 0.0;
+                        for (int v = 0; v < M; ++v) W[v] = R(0);
 #pragma unroll
                         for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz)
 #pragma unroll
                             for (int dy = (D > 1 ? -1 : 0); dy <= (D > 1 ? 1 : 0); ++dy)
 #pragma unroll
                                 for (int dx = -1; dx <= 1; ++dx) {
-                                    const double w = ((D > 2 ? pw(az, dz) : 1.0) * (D > 1 ? pw(ay, dy) : 1.0)) *
-                                                     pw(ax, dx);
+                                    const R w = R((D > 2 ? pw(az, dz) : 1.0) * (D > 1 ? pw(ay, dy) : 1.0)) *
+                                                R(pw(ax, dx));
                                     const int bs = bl + dz * SZ + dy * SY + dx;
 #pragma unroll
                                     for (int v = 0; v < M; ++v) W[v] += w * sW[v][bs];
@@ -630,8 +630,8 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
 #pragma unroll
                         for (int v = 0; v < M; ++v) P4[i][v] = sFine[r][v][task];
                     } else {
-                        double W[M];
-                        value_at<D, M>(g, x, u + 1, p, W);
+                        R W[M];
+                        value_at<D, M, R, R>(g, x, u + 1, p, W);
                         recon_vars<EQ, D, M, R>(g, W, P4[i]);
                     }
                 }
@@ -669,12 +669,12 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
         const int b = bz * SZ + by * SY + bx;
         if (tile_leaf(bx, by, bz)) {
         const long long id = cell_id(g, u, ox + i, oy + j, oz + kz);
-        double self[M], f[M], q0p[M];
+        R self[M], f[M], q0p[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) self[v] = sW[v][b];
 #pragma unroll
         for (int v = 0; v < M; ++v) q0p[v] = s >= 2 ? sQ0[v][tid] : self[v]; // the stage value is the staged exposure
-        source<EQ, M>(g, self, f);
+        source<EQ, M, R>(g, self, f);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             const int stride = k == 0 ? 1 : (k == 1 ? SY : SZ);
@@ -699,15 +699,15 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
                 Fm[v] = double(sF[v][fm]);
                 Fp[v] = double(sF[v][fp]);
             }
-            const double idx = g.rdx[u][k];
+            const R idx = R(g.rdx[u][k]);
 #pragma unroll
-            for (int v = 0; v < M; ++v) f[v] += (Fm[v] - Fp[v]) * idx;
+            for (int v = 0; v < M; ++v) f[v] += (R(Fm[v]) - R(Fp[v])) * idx;
             if (reg) {
                 reg_add<M>(g, u, id, 2 * k, km, bw, Fm);
                 reg_add<M>(g, u, id, 2 * k + 1, kp, bw, Fp);
             }
         }
-        rk_update<M>(g, u, id, s, dtl, f, q0p, self);
+        rk_update<M, R>(g, u, id, s, R(dtl), f, q0p, self);
         }
     }
     __syncthreads(); // shared arrays are reused by the next tile

@@ -1,7 +1,7 @@
-// mrlt_stage_eq.cu -- instantiates the stage and macro-step kernels of one equation,
+// mrlt_stage_eq.cu -- instantiates the stage kernels of one equation,
 // selected by MRLT_STAGE_EQ (0 advection, 1 Burgers, 2 Euler, 3 reaction-
 // diffusion) at compile time, for d = 1, 2, 3 and both flux precisions.
-#include "mrlt_macro.cuh"
+#include "mrlt_stage.cuh"
 
 #ifndef MRLT_STAGE_EQ
 #error "compile with -DMRLT_STAGE_EQ=<equation id>"
@@ -26,18 +26,6 @@ int launch_stage_eq<MRLT_STAGE_EQ>(const Grid& g, cudaStream_t st, int lo, int h
                       : stage_dispatch<E, 3, double>(g, st, lo, hi, s, lmin, b, reg);
     default:
         return 0;
-    }
-}
-
-template <>
-int launch_macro_eq<MRLT_STAGE_EQ>(const Grid& g, cudaStream_t st, const MacroArgs* a)
-{
-    constexpr int E = MRLT_STAGE_EQ;
-    switch (g.d) {
-    case 1: return g.prec ? macro_dispatch<E, 1, float>(g, st, a) : macro_dispatch<E, 1, double>(g, st, a);
-    case 2: return g.prec ? macro_dispatch<E, 2, float>(g, st, a) : macro_dispatch<E, 2, double>(g, st, a);
-    case 3: return g.prec ? macro_dispatch<E, 3, float>(g, st, a) : macro_dispatch<E, 3, double>(g, st, a);
-    default: return -1;
     }
 }
 

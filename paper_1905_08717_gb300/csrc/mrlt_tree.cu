@@ -23,24 +23,26 @@ static inline int blocks_list(const Grid& g, int l)
 // ------------------------------------------------------------ kernels
 // Each kernel waits for its predecessor (programmatic dependent launch) and
 // runs one device body of mrlt_tree_dev.cuh over its own grid.
+// (T: the storage type of the fields, double or float)
+template <class T>
 __global__ void k_leaf_copy(const __grid_constant__ Grid g, int lo, int hi, int from, int to)
 {
     pdl_enter();
-    dev_leaf_copy(g, lo, hi, from, to);
+    dev_leaf_copy<T>(g, lo, hi, from, to);
 }
 
-template <int D>
+template <int D, class T>
 __global__ void k_project(const __grid_constant__ Grid g, int l, int mode)
 {
     pdl_enter();
-    dev_project<D>(g, l, mode);
+    dev_project<D, T>(g, l, mode);
 }
 
-template <int D, int M>
+template <int D, int M, class T>
 __global__ void k_detail(const __grid_constant__ Grid g, int lo, int hi)
 {
     pdl_enter();
-    dev_detail<D, M>(g, lo, hi);
+    dev_detail<D, M, T>(g, lo, hi);
 }
 
 template <int D>
@@ -64,11 +66,11 @@ __global__ void k_close(const __grid_constant__ Grid g, int l)
     dev_close<D>(g, l);
 }
 
-template <int D, int M>
+template <int D, int M, class T>
 __global__ void k_apply(const __grid_constant__ Grid g, int l, int la)
 {
     pdl_enter();
-    dev_apply<D, M>(g, l, la);
+    dev_apply<D, M, T>(g, l, la);
 }
 
 // compaction of levels lo..hi: chunks of NTHREADS cells, one block each
@@ -98,27 +100,30 @@ __global__ void k_tile_list(const __grid_constant__ Grid g, int lo)
     level_tile_list<1024>(g, lo + blockIdx.x);
 }
 
-template <int D>
+template <int D, class T>
 __global__ void k_reflux(const __grid_constant__ Grid g, int lo, int hi)
 {
     pdl_enter();
-    dev_reflux<D>(g, lo, hi);
+    dev_reflux<D, T>(g, lo, hi);
 }
 
 // ------------------------------------------------------------ reductions
+template <class T>
 __global__ void k_scale(const __grid_constant__ Grid g, int l)
 {
     pdl_enter();
-    dev_scale(g, l, l);
+    dev_scale<T>(g, l, l);
 }
 
+template <class T>
 __global__ void k_finite(const __grid_constant__ Grid g, int l)
 {
     pdl_enter();
-    dev_finite(g, l, l);
+    dev_finite<T>(g, l, l);
 }
 
 // fixed-shape partial sums (deterministic): part[block * m + v]
+template <class T>
 __global__ void k_mass(Grid g, int l, double* part)
 {
     pdl_enter();
@@ -131,7 +136,7 @@ __global__ void k_mass(Grid g, int l, double* part)
         for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
              t += (long long)gridDim.x * blockDim.x) {
             const long long id = list[t];
-            if (id >= 0 && id < N) acc += fbase(g, F_QE, l)[v * N + id];
+            if (id >= 0 && id < N) acc += double(fld<T>(g, F_QE, l)[v * N + id]);
         }
         sh[threadIdx.x] = acc;
         __syncthreads();
@@ -144,6 +149,7 @@ __global__ void k_mass(Grid g, int l, double* part)
     }
 }
 
+template <class T>
 __global__ void k_pack(Grid g, int l, long long base, int* keys, double* vals)
 {
     pdl_enter();
@@ -164,14 +170,14 @@ __global__ void k_pack(Grid g, int l, long long base, int* keys, double* vals)
             K[3] = c[2];
         }
         if (vals)
-            for (int v = 0; v < g.m; ++v) vals[(base + t) * g.m + v] = fbase(g, F_QE, l)[v * N + id];
+            for (int v = 0; v < g.m; ++v) vals[(base + t) * g.m + v] = double(fld<T>(g, F_QE, l)[v * N + id]);
     }
 }
 
 // inverse MR transform onto the finest level, in scratch pyramids T / us:
 // bottom-up projection of the leaves' q^{n+1} into internal nodes, then
 // top-down prediction of every absent cell from the level above
-template <int D>
+template <int D, class F>
 __global__ void k_uni_up(Grid g, int l, double* T, uint8_t* us)
 {
     pdl_enter();
@@ -184,7 +190,7 @@ __global__ void k_uni_up(Grid g, int l, double* T, uint8_t* us)
         const int s = status(g, l, id);
         us[g.off[l] + id] = s != 0;
         if (s == 1) {
-            for (int v = 0; v < g.m; ++v) Tl[v * N + id] = fbase(g, F_QE, l)[v * N + id];
+            for (int v = 0; v < g.m; ++v) Tl[v * N + id] = double(fld<F>(g, F_QE, l)[v * N + id]);
         } else if (s == 2) {
             int c[3];
             cell_xyz(g, l, id, c);
@@ -231,24 +237,37 @@ __global__ void k_uni_down(Grid g, int l, double* T, uint8_t* us)
 }
 
 // ------------------------------------------------------------ launchers
-template <int D>
+template <int D, class T>
 static void project_d(Launcher& L, int l, int mode)
 {
-    pdl_launch(k_project<D>, blocks_list(L.g, l), NTHREADS, 0, L.st, L.g, l, mode);
+    pdl_launch(k_project<D, T>, blocks_list(L.g, l), NTHREADS, 0, L.st, L.g, l, mode);
 }
+
+// a kernel template of the fields' storage type: float in the mixed mode
+#define MRLT_T_DISPATCH(fn, ...)              \
+    do {                                      \
+        if (g.prec) fn<float>(__VA_ARGS__);   \
+        else fn<double>(__VA_ARGS__);         \
+    } while (0)
 
 void Launcher::project(int l, int mode)
 {
     ++n;
-    if (g.d == 1) project_d<1>(*this, l, mode);
-    else if (g.d == 2) project_d<2>(*this, l, mode);
-    else project_d<3>(*this, l, mode);
+    if (g.d == 1) g.prec ? project_d<1, float>(*this, l, mode) : project_d<1, double>(*this, l, mode);
+    else if (g.d == 2) g.prec ? project_d<2, float>(*this, l, mode) : project_d<2, double>(*this, l, mode);
+    else g.prec ? project_d<3, float>(*this, l, mode) : project_d<3, double>(*this, l, mode);
+}
+
+template <class T>
+static void leaf_copy_t(Launcher& L, int lo, int hi, int from, int to)
+{
+    pdl_launch(k_leaf_copy<T>, blocks_list(L.g, hi), NTHREADS, 0, L.st, L.g, lo, hi, from, to);
 }
 
 void Launcher::leaf_copy(int lo, int hi, int from, int to)
 {
     ++n;
-    pdl_launch(k_leaf_copy, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi, from, to);
+    MRLT_T_DISPATCH(leaf_copy_t, *this, lo, hi, from, to);
 }
 
 template <int D, int M>
@@ -256,7 +275,8 @@ static void adapt_dm(Launcher& L, int la)
 {
     const Grid& g = L.g;
     const int hi = g.L - 1; // levels whose nodes may own children
-    pdl_launch(k_detail<D, M>, blocks_list(g, hi), NTHREADS, 0, L.st, g, la, hi);
+    if (g.prec) pdl_launch(k_detail<D, M, float>, blocks_list(g, hi), NTHREADS, 0, L.st, g, la, hi);
+    else pdl_launch(k_detail<D, M, double>, blocks_list(g, hi), NTHREADS, 0, L.st, g, la, hi);
     pdl_launch(k_desire<D>, blocks_dense(g.N[hi]), NTHREADS, 0, L.st, g, la, hi, la);
     pdl_launch(k_allow<D>, blocks_dense(g.N[hi]), NTHREADS, 0, L.st, g, la, hi, la);
     L.n += 3;
@@ -267,7 +287,10 @@ template <int D, int M>
 static void apply_dm(Launcher& L, int la)
 {
     const Grid& g = L.g;
-    for (int l = la; l <= g.L; ++l, ++L.n) pdl_launch(k_apply<D, M>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
+    for (int l = la; l <= g.L; ++l, ++L.n) {
+        if (g.prec) pdl_launch(k_apply<D, M, float>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
+        else pdl_launch(k_apply<D, M, double>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
+    }
 }
 
 #define MRLT_DM_DISPATCH(fn, ...)                                   \
@@ -303,12 +326,19 @@ void Launcher::compact(int lo, int hi)
     n += 4;
 }
 
+template <class T>
+static void reflux_t(Launcher& L, int lo, int hi)
+{
+    const Grid& g = L.g;
+    if (g.d == 1) pdl_launch(k_reflux<1, T>, blocks_list(g, hi), NTHREADS, 0, L.st, g, lo, hi);
+    else if (g.d == 2) pdl_launch(k_reflux<2, T>, blocks_list(g, hi), NTHREADS, 0, L.st, g, lo, hi);
+    else pdl_launch(k_reflux<3, T>, blocks_list(g, hi), NTHREADS, 0, L.st, g, lo, hi);
+}
+
 void Launcher::reflux(int lo, int hi)
 {
     ++n;
-    if (g.d == 1) pdl_launch(k_reflux<1>, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi);
-    else if (g.d == 2) pdl_launch(k_reflux<2>, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi);
-    else pdl_launch(k_reflux<3>, blocks_list(g, hi), NTHREADS, 0, st, g, lo, hi);
+    MRLT_T_DISPATCH(reflux_t, *this, lo, hi);
 }
 
 __global__ void k_scale_init(Grid g)
@@ -326,6 +356,7 @@ __global__ void k_set_dt(Grid g, double dt)
 // leaf values from (level, i, j, k) keys: q^n and the end value of each leaf
 // (restoring a state saved at a macro-step boundary); a key that is not a
 // leaf of the installed tree sets ERR_INDEX
+template <class T>
 __global__ void k_set_leaves(Grid g, const int* keys, const double* vals, long long n)
 {
     pdl_enter();
@@ -344,15 +375,31 @@ __global__ void k_set_leaves(Grid g, const int* keys, const double* vals, long l
             continue;
         }
         const long long N = g.N[l];
-        double* q0 = fbase_w(g, F_Q0, l) + id;
-        double* qe = fbase_w(g, F_QE, l) + id;
-        for (int v = 0; v < g.m; ++v) q0[v * N] = qe[v * N] = vals[t * g.m + v];
+        T* q0 = fld<T>(g, F_Q0, l) + id;
+        T* qe = fld<T>(g, F_QE, l) + id;
+        for (int v = 0; v < g.m; ++v) q0[v * N] = qe[v * N] = T(vals[t * g.m + v]);
     }
 }
 
 void Launcher::set_leaves(const int* keys, const double* vals, long long count)
 {
-    pdl_launch(k_set_leaves, blocks_dense(count), NTHREADS, 0, st, g, keys, vals, count);
+    if (g.prec) pdl_launch(k_set_leaves<float>, blocks_dense(count), NTHREADS, 0, st, g, keys, vals, count);
+    else pdl_launch(k_set_leaves<double>, blocks_dense(count), NTHREADS, 0, st, g, keys, vals, count);
+    ++n;
+}
+
+// finest-level data uploaded as double, stored in the field's type
+__global__ void k_store_finest(Grid g, const double* src)
+{
+    pdl_enter();
+    const long long n = g.N[g.L] * g.m;
+    float* dst = static_cast<float*>(g.f[F_Q0]) + g.off[g.L] * g.m;
+    GRID_STRIDE(i, n) dst[i] = float(src[i]);
+}
+
+void Launcher::store_finest(const double* src)
+{
+    pdl_launch(k_store_finest, blocks_dense(g.N[g.L] * g.m), NTHREADS, 0, st, g, src);
     ++n;
 }
 
@@ -371,29 +418,40 @@ void Launcher::set_dt(double dt)
 void Launcher::scale(int l)
 {
     ++n;
-    k_scale<<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
+    if (g.prec) k_scale<float><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
+    else k_scale<double><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
 }
 void Launcher::finite(int l)
 {
     ++n;
-    k_finite<<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
+    if (g.prec) k_finite<float><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
+    else k_finite<double><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l);
 }
 void Launcher::mass(int l, double* part)
 {
     ++n;
-    k_mass<<<MASS_BLOCKS, NTHREADS, 0, st>>>(g, l, part);
+    if (g.prec) k_mass<float><<<MASS_BLOCKS, NTHREADS, 0, st>>>(g, l, part);
+    else k_mass<double><<<MASS_BLOCKS, NTHREADS, 0, st>>>(g, l, part);
 }
 void Launcher::pack(int l, long long base, int* keys, double* vals)
 {
     ++n;
-    k_pack<<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l, base, keys, vals);
+    if (g.prec) k_pack<float><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l, base, keys, vals);
+    else k_pack<double><<<blocks_list(g, l), NTHREADS, 0, st>>>(g, l, base, keys, vals);
 }
 void Launcher::uniform(double* T, uint8_t* us)
 {
     for (int l = g.L; l >= g.lb; --l, ++n) {
-        if (g.d == 1) k_uni_up<1><<<blocks_dense(g.N[l]), NTHREADS, 0, st>>>(g, l, T, us);
-        else if (g.d == 2) k_uni_up<2><<<blocks_dense(g.N[l]), NTHREADS, 0, st>>>(g, l, T, us);
-        else k_uni_up<3><<<blocks_dense(g.N[l]), NTHREADS, 0, st>>>(g, l, T, us);
+        const int nb = blocks_dense(g.N[l]);
+        if (g.prec) {
+            if (g.d == 1) k_uni_up<1, float><<<nb, NTHREADS, 0, st>>>(g, l, T, us);
+            else if (g.d == 2) k_uni_up<2, float><<<nb, NTHREADS, 0, st>>>(g, l, T, us);
+            else k_uni_up<3, float><<<nb, NTHREADS, 0, st>>>(g, l, T, us);
+        } else {
+            if (g.d == 1) k_uni_up<1, double><<<nb, NTHREADS, 0, st>>>(g, l, T, us);
+            else if (g.d == 2) k_uni_up<2, double><<<nb, NTHREADS, 0, st>>>(g, l, T, us);
+            else k_uni_up<3, double><<<nb, NTHREADS, 0, st>>>(g, l, T, us);
+        }
     }
     for (int l = g.lb + 1; l <= g.L; ++l, ++n) {
         if (g.d == 1) k_uni_down<1><<<blocks_dense(g.N[l]), NTHREADS, 0, st>>>(g, l, T, us);

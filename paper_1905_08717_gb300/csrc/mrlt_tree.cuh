@@ -22,6 +22,7 @@ struct Launcher {
     void scale_init();                                 // running max |q_v| := 1e-14
     void set_dt(double dt);                            // *g.dtp := dt
     void set_leaves(const int* keys, const double* vals, long long count); // leaf q^n and end values
+    void store_finest(const double* src); // finest-level q^n from double data (float fields)
     void finite(int l);
     void mass(int l, double* part);
     void pack(int l, long long base, int* keys, double* vals);

@@ -17,14 +17,17 @@ enum ProjMode { PM_Q0 = 0, PM_Q1, PM_Q2, PM_REF2, PM_PRJ2, PM_REF3, PM_PRJ3, PM_
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
 // ------------------------------------------------------------ simple leaf copies
-static __device__ __forceinline__ void dev_leaf_copy(const Grid& g, int lo, int hi, int from, int to)
+// T: storage type of the fields (double, or float in the mixed mode); the
+// arithmetic of a body is in T except where it says otherwise
+template <class T>
+__device__ __forceinline__ void dev_leaf_copy(const Grid& g, int lo, int hi, int from, int to)
 {
     for (int l = lo; l <= hi; ++l) {
         const int cnt = g.counts[l];
         const int* list = g.leaves + g.off[l];
         const long long N = g.N[l];
-        const double* a = fbase(g, from, l);
-        double* b = fbase_w(g, to, l);
+        const T* a = fld<T>(g, from, l);
+        T* b = fld<T>(g, to, l);
         MRLT_GRID_STRIDE(t, cnt)
         {
             const long long id = list[t];
@@ -46,7 +49,7 @@ static __device__ __forceinline__ void dev_leaf_copy(const Grid& g, int lo, int 
 //  PM_PRJ3: Alg. 6 -- q** = mean(children at t^n + dt_{l+1}), end value
 //           2 q** - q^n (Eq. 16 with the theta values implied by q**)
 //  PM_MID:  Alg. 3 / Sec. 4.3 refresh of the mid-step level lmin-1
-template <int D>
+template <int D, class T>
 __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
 {
     const int cnt = g.counts[LMAX + 1 + l];
@@ -70,63 +73,63 @@ __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
                             D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
             cst[k] = status(g, l + 1, ch[k]);
         }
-        const double* c0 = fbase(g, F_Q0, l + 1);
-        const double* c1 = fbase(g, F_Q1, l + 1);
-        const double* c2 = fbase(g, F_Q2, l + 1);
-        const double* ce = fbase(g, F_QE, l + 1);
-        double* q0 = fbase_w(g, F_Q0, l);
-        double* q1 = fbase_w(g, F_Q1, l);
-        double* q2 = fbase_w(g, F_Q2, l);
-        double* qe = fbase_w(g, F_QE, l);
+        const T* c0 = fld<T>(g, F_Q0, l + 1);
+        const T* c1 = fld<T>(g, F_Q1, l + 1);
+        const T* c2 = fld<T>(g, F_Q2, l + 1);
+        const T* ce = fld<T>(g, F_QE, l + 1);
+        T* q0 = fld<T>(g, F_Q0, l);
+        T* q1 = fld<T>(g, F_Q1, l);
+        T* q2 = fld<T>(g, F_Q2, l);
+        T* qe = fld<T>(g, F_QE, l);
         for (int v = 0; v < g.m; ++v) {
             const long long o = v * N + id;
-            double acc = 0.0;
+            T acc = T(0);
 #pragma unroll
             for (int k = 0; k < NCH; ++k) {
                 const long long oc = v * Nc + ch[k];
-                double w;
+                T w;
                 switch (mode) {
                 case PM_Q0: w = c0[oc]; break;
                 case PM_Q1: case PM_REF2: w = c1[oc]; break;
                 case PM_Q2: case PM_REF3: w = c2[oc]; break;
                 case PM_PRJ2:
-                    if (cst[k] == 1) w = g.rk == 2 ? 2.0 * ce[oc] - c0[oc] : 4.0 * c2[oc] - 3.0 * c0[oc];
-                    else w = 2.0 * c1[oc] - c0[oc];
+                    if (cst[k] == 1) w = g.rk == 2 ? T(2) * ce[oc] - c0[oc] : T(4) * c2[oc] - T(3) * c0[oc];
+                    else w = T(2) * c1[oc] - c0[oc];
                     break;
                 case PM_PRJ3: w = ce[oc]; break;
                 default: w = c0[oc]; break; // PM_MID: children at t^n
                 }
                 acc += w;
             }
-            const double mean = acc * (1.0 / NCH);
+            const T mean = acc * T(1.0 / NCH);
             switch (mode) {
             case PM_Q0: q0[o] = mean; break;
             case PM_Q1: case PM_PRJ2: q1[o] = mean; break;
             case PM_Q2: q2[o] = mean; break;
             case PM_REF2:
-                fbase_w(g, F_XH, l)[o] = mean;
-                q1[o] = 2.0 * mean - q0[o];
+                fld<T>(g, F_XH, l)[o] = mean;
+                q1[o] = T(2) * mean - q0[o];
                 break;
             case PM_REF3: {
-                fbase_w(g, F_N1, l)[o] = mean;
-                fbase_w(g, F_N3, l)[o] = -6.5 * q0[o] - 1.5 * q1[o] + 9.0 * mean;
-                q2[o] = -5.5 * q0[o] - 1.5 * q1[o] + 8.0 * mean;
+                fld<T>(g, F_N1, l)[o] = mean;
+                fld<T>(g, F_N3, l)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * mean;
+                q2[o] = T(-5.5) * q0[o] - T(1.5) * q1[o] + T(8) * mean;
                 break;
             }
             case PM_PRJ3:
                 q2[o] = mean;
-                qe[o] = 2.0 * mean - q0[o];
+                qe[o] = T(2) * mean - q0[o];
                 break;
             default: { // PM_MID
                 if (g.rk == 2) {
-                    fbase_w(g, F_NH, l)[o] = mean;
-                    qe[o] = -2.0 * q0[o] - q1[o] + 4.0 * mean;
+                    fld<T>(g, F_NH, l)[o] = mean;
+                    qe[o] = T(-2) * q0[o] - q1[o] + T(4) * mean;
                 } else {
                     q2[o] = mean;
-                    qe[o] = 2.0 * mean - q0[o];
-                    const double n1 = (mean + 5.5 * q0[o] + 1.5 * q1[o]) * 0.125;
-                    fbase_w(g, F_N1, l)[o] = n1;
-                    fbase_w(g, F_N3, l)[o] = -6.5 * q0[o] - 1.5 * q1[o] + 9.0 * n1;
+                    qe[o] = T(2) * mean - q0[o];
+                    const T n1 = (mean + T(5.5) * q0[o] + T(1.5) * q1[o]) * T(0.125);
+                    fld<T>(g, F_N1, l)[o] = n1;
+                    fld<T>(g, F_N3, l)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * n1;
                 }
             }
             }
@@ -142,8 +145,9 @@ __device__ __forceinline__ double eps_level(const Grid& g, int l)
 
 // detail norm (Eq. 5) of every internal node of levels lo..hi (< L): max over
 // children and variables of |q_child - prediction| / s_v; flags significance
-// (> eps_{l+1}) and the scale-safety bound (> 8 eps_{l+1})
-template <int D, int M>
+// (> eps_{l+1}) and the scale-safety bound (> 8 eps_{l+1}).  The predictions
+// and the test are FP64 whatever the storage type T.
+template <int D, int M, class T>
 __device__ __forceinline__ void dev_detail(const Grid& g, int lo, int hi)
 {
     double sc[M];
@@ -170,14 +174,14 @@ __device__ __forceinline__ void dev_detail(const Grid& g, int lo, int hi)
                 const Ctx x{l, 0, g.lb};
                 double nrm = 0.0;
                 double p[1 << D][M];
-                predict_children<D, M>(g, x, l, c, p);
+                predict_children<D, M, T>(g, x, l, c, p);
 #pragma unroll
                 for (int k = 0; k < (1 << D); ++k) {
                     const long long cid = cell_id(g, l + 1, 2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
                                                   D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
-                    const double* qc = fbase(g, F_Q0, l + 1) + cid;
+                    const T* qc = fld<T>(g, F_Q0, l + 1) + cid;
 #pragma unroll
-                    for (int v = 0; v < M; ++v) nrm = fmax(nrm, fabs(qc[v * Nc] - p[k][v]) / sc[v]);
+                    for (int v = 0; v < M; ++v) nrm = fmax(nrm, fabs(double(qc[v * Nc]) - p[k][v]) / sc[v]);
                 }
                 if (fabs(nrm - el) <= 1e-10 * el || fabs(nrm - 8.0 * el) <= 8e-10 * el)
                     atomicAdd(g.near, 1ull);
@@ -322,9 +326,10 @@ __device__ __forceinline__ void dev_close(const Grid& g, int l)
 }
 
 // install the new tree on level l (top-down): status from the refinement
-// flags; new nodes predicted from level l-1 (Sec. 2); new leaves and merged
-// nodes get q^{n+1} = q^n; registers of changed nodes cleared
-template <int D, int M>
+// flags; new nodes predicted from level l-1 (Sec. 2, in FP64, stored as T);
+// new leaves and merged nodes get q^{n+1} = q^n; registers of changed nodes
+// cleared
+template <int D, int M, class T>
 __device__ __forceinline__ void dev_apply(const Grid& g, int l, int la)
 {
     const long long N = g.N[l];
@@ -344,16 +349,16 @@ __device__ __forceinline__ void dev_apply(const Grid& g, int l, int la)
         const uint8_t nw = exists ? (refined ? 2 : 1) : 0;
         if (nw == old) continue;
         g.st[g.off[l] + id] = nw;
-        double* q0 = fbase_w(g, F_Q0, l) + id;
+        T* q0 = fld<T>(g, F_Q0, l) + id;
         if (old == 0 && nw != 0) {
             const Ctx x{l, 0, g.lb};
             double p[M];
-            predict<D, M>(g, x, l, c, p);
+            predict<D, M, T, double>(g, x, l, c, p);
 #pragma unroll
-            for (int v = 0; v < M; ++v) q0[v * N] = p[v];
+            for (int v = 0; v < M; ++v) q0[v * N] = T(p[v]);
         }
         if (nw == 1) {
-            double* qe = fbase_w(g, F_QE, l) + id;
+            T* qe = fld<T>(g, F_QE, l) + id;
 #pragma unroll
             for (int v = 0; v < M; ++v) qe[v * N] = q0[v * N];
         }
@@ -535,7 +540,7 @@ __device__ __forceinline__ void level_tile_list(const Grid& g, int l)
 // conservative correction of the coarse leaves of level l whose step ended:
 // q += +-(coarse time-integrated flux - mean of the fine ones) / dx; the
 // registers read are cleared for the next step
-template <int D>
+template <int D, class T>
 __device__ __forceinline__ void dev_reflux(const Grid& g, int lo, int hi)
 {
     for (int l = lo; l <= hi; ++l) {
@@ -575,7 +580,7 @@ __device__ __forceinline__ void dev_reflux(const Grid& g, int lo, int hi)
                 }
                 double* rc = g.rc + g.off[l] * g.nf * m + id;
                 double* rf = g.rf + g.off[l + 1] * g.nf * m;
-                double* qe = fbase_w(g, F_QE, l) + id;
+                T* qe = fld<T>(g, F_QE, l) + id;
                 const double idx = 1.0 / g.dx[l][k];
                 for (int v = 0; v < m; ++v) {
                     double sum = 0.0;
@@ -585,7 +590,8 @@ __device__ __forceinline__ void dev_reflux(const Grid& g, int lo, int hi)
                         *r = 0.0;
                     }
                     double* r = rc + (long long)(fi * m + v) * N;
-                    qe[v * N] += side * (*r - sum * (1.0 / NT)) * idx;
+                    // the correction from the FP64 registers, rounded to T once
+                    qe[v * N] = T(double(qe[v * N]) + side * (*r - sum * (1.0 / NT)) * idx);
                     *r = 0.0;
                 }
             }
@@ -595,7 +601,8 @@ __device__ __forceinline__ void dev_reflux(const Grid& g, int lo, int hi)
 
 // ------------------------------------------------------------ reductions
 // running max |q^n_v| over the leaves of levels lo..hi (detail normalisation)
-static __device__ __forceinline__ void dev_scale(const Grid& g, int lo, int hi)
+template <class T>
+__device__ __forceinline__ void dev_scale(const Grid& g, int lo, int hi)
 {
     for (int l = lo; l <= hi; ++l) {
         const int cnt = g.counts[l];
@@ -606,7 +613,7 @@ static __device__ __forceinline__ void dev_scale(const Grid& g, int lo, int hi)
         {
             const long long id = list[t];
             if (id < 0 || id >= N) continue;
-            for (int v = 0; v < g.m; ++v) mx[v] = fmax(mx[v], fabs(fbase(g, F_Q0, l)[v * N + id]));
+            for (int v = 0; v < g.m; ++v) mx[v] = fmax(mx[v], fabs(double(fld<T>(g, F_Q0, l)[v * N + id])));
         }
         for (int v = 0; v < g.m; ++v) {
             double a = mx[v];
@@ -618,7 +625,8 @@ static __device__ __forceinline__ void dev_scale(const Grid& g, int lo, int hi)
 }
 
 // non-finite end values of the leaves of levels lo..hi set ERR_NONFINITE
-static __device__ __forceinline__ void dev_finite(const Grid& g, int lo, int hi)
+template <class T>
+__device__ __forceinline__ void dev_finite(const Grid& g, int lo, int hi)
 {
     for (int l = lo; l <= hi; ++l) {
         const int cnt = g.counts[l];
@@ -629,14 +637,14 @@ static __device__ __forceinline__ void dev_finite(const Grid& g, int lo, int hi)
             const long long id = list[t];
             if (id < 0 || id >= N) continue;
             for (int v = 0; v < g.m; ++v)
-                if (!isfinite(fbase(g, F_QE, l)[v * N + id])) atomicOr(g.err, ERR_NONFINITE);
+                if (!isfinite(double(fld<T>(g, F_QE, l)[v * N + id]))) atomicOr(g.err, ERR_NONFINITE);
         }
     }
 }
 
 // largest sum of characteristic speeds over the leaves of levels lo..hi (CFL
 // step), as the bit pattern of a positive double in *g.wmax
-template <int EQ, int D>
+template <int EQ, int D, class T>
 __device__ __forceinline__ void dev_wave(const Grid& g, int lo, int hi)
 {
     constexpr int M = EQ == 2 ? D + 2 : 1;
@@ -649,10 +657,10 @@ __device__ __forceinline__ void dev_wave(const Grid& g, int lo, int hi)
         {
             const long long id = list[t];
             if (id < 0 || id >= N) continue;
-            const double* qe = fbase(g, F_QE, l) + id;
+            const T* qe = fld<T>(g, F_QE, l) + id;
             double q[M];
 #pragma unroll
-            for (int v = 0; v < M; ++v) q[v] = qe[v * N];
+            for (int v = 0; v < M; ++v) q[v] = double(qe[v * N]);
             const double s = wave_speed<EQ, D, M>(g, q);
             w = fmax(w, s != s ? 1e300 : s);
         }

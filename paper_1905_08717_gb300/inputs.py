@@ -38,7 +38,7 @@ FLUX_DEFAULT = 0
 FLUX_AUSM_PLUS = 1
 
 PREC_FP64 = 0
-PREC_MIXED = 1   # FP32 face fluxes; state, registers and adaptation FP64
+PREC_MIXED = 1   # FP32 state, fluxes and stage updates; registers and detail test FP64
 
 
 @dataclass
