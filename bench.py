@@ -148,19 +148,36 @@ def _fp64_peak_tflops(torch) -> float:
     return 2.0 * n ** 3 / best / 1e12
 
 
+STAGE_SOURCES = ("mrlt_impl.cuh", "mrlt_stage.cuh")
+
+
+def stage_kernel_hash() -> str:
+    """sha256 (first 16 hex digits) of the stage kernel's sources: a DRAM figure
+    recorded under profiles/ applies only to the kernel it was measured on"""
+    import hashlib
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1905_08717_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_per_leaf_stage():
     """DRAM bytes per leaf-stage of the stage kernel from the committed ncu
-    summary (None if absent or taken on another kernel version)."""
+    summary; None if absent or recorded for another version of the kernel
+    (its `kernel_sha16:` line differs from the sources built here)."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_dram_euler2d_L10.md")
     if not os.path.exists(path):
         return None
+    val, sha = None, None
     for ln in open(path):
         if ln.startswith("dram_bytes_per_leaf_stage:"):
             try:
-                return float(ln.split(":")[1].split()[0])
+                val = float(ln.split(":")[1].split()[0])
             except ValueError:
                 return None
-    return None
+        elif ln.startswith("kernel_sha16:"):
+            sha = ln.split(":")[1].strip()
+    return val if sha == stage_kernel_hash() else None
 
 
 def _uniform_roofline(pkg, inputs, torch, peak: float, iters: int = 20) -> dict:
@@ -382,6 +399,102 @@ def _serving(pkg, inputs, torch, n: int = 200, rate: float = 200.0) -> dict:
     return out
 
 
+def _mixed_vs_oracle(pkg, inputs, case: str, L: int, t_end: float) -> dict:
+    """L1 error of rho of the mixed-precision GPU solve (and of the FP64 GPU
+    solve) against the FP64 oracle over a whole solve at a size the oracle
+    finishes in seconds, relative to the oracle's L1 norm of rho."""
+    import numpy as np
+    import oracle
+    if case == "euler2d":
+        p, q = inputs.euler_2d_quadrants(L=L, eps=1e-3, seed=0)
+    else:
+        p, q = inputs.euler_3d_blast(L=L, eps=1e-3, min_level=3, precision=inputs.PREC_FP64)
+    p = p.replace(precision=inputs.PREC_FP64)
+    ref = oracle.Oracle(p, q)
+    ref.step(t_end)
+    u_o = ref.uniform()[0]
+    out = {"workload": f"{case} L={L} eps=1e-3 t={t_end}", "oracle_iters": ref.stats()["iters"]}
+    ref.close()
+    for key, prec in (("mixed", inputs.PREC_MIXED), ("fp64", inputs.PREC_FP64)):
+        g = pkg.Solver(p.replace(precision=prec), q)
+        g.step(t_end)
+        u = g.uniform()[0]
+        g.close()
+        out[f"rel_l1_rho_{key}"] = float(np.abs(u - u_o).sum() / np.abs(u_o).sum())
+    return out
+
+
+def _precision_3d(pkg, inputs, torch, L: int = 8, t_end: float = 0.1) -> dict:
+    """The 3D Euler blast (rho = 1, p = 1, p = 10 inside r < 0.1, walls), L = 8
+    (256^3 finest), eps = 1e-3, RK3 LT/NERK to t = 0.1, in FP64 and in the
+    mixed mode: solve time, leaf updates/s, the stage kernel's algorithmic HBM
+    rate (state bytes of every leaf-stage / summed CUDA-event time of the stage
+    launches), the mixed-vs-FP64 L1 distance of rho, and both against the
+    FP64 oracle at L = 6 (whole solve)."""
+    import numpy as np
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    p, q = inputs.euler_3d_blast(L=L, eps=1e-3, min_level=3)
+    out = {"workload": f"euler3d blast L={L} (256^3), eps=1e-3, rk3 lt/nerk, t=0..{t_end}"}
+    u = {}
+    for key, prec, esz in (("fp64", inputs.PREC_FP64, 8), ("mixed", inputs.PREC_MIXED, 4)):
+        s = pkg.Solver(p.replace(precision=prec), q)
+        s.step(0.005)  # warm-up (graph capture)
+        ts = []
+        for _ in range(2):
+            s.reset(q)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.step(t_end)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        st = s.stats()
+        u[key] = s.uniform()[0]
+        # stage kernel: one more profiled solve (CUDA events around each stage launch)
+        s.reset(q)
+        s.profile(True)
+        s.step(t_end)
+        pr = s.profile_read()
+        s.profile(False)
+        s.close()
+        ls = pr["leaf_stages"]
+        nbytes = (2 * float(ls[0]) + 3 * float(ls[1] + ls[2])) * 5 * esz
+        sec = pr["stage_ms"] / 1e3
+        out[key] = {"ms_per_solve": 1e3 * min(ts), "leaf_updates": st["updates"],
+                    "updates_per_s": st["updates"] / min(ts), "leaves_at_t_end": st["leaves"],
+                    "stage_kernel": {"achieved_gbs": nbytes / sec / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                                     "frac": nbytes / sec / 1e9 / peaks["hbm_gbs"],
+                                     "launches": pr["stage_launches"],
+                                     "leaf_stages_per_launch": float(ls.sum()) / max(pr["stage_launches"], 1),
+                                     "bytes_per_leaf_stage": f"stage 1: 2 x 5 x {esz}, stages 2-3: 3 x 5 x {esz}"}}
+    out["rel_l1_rho_mixed_vs_fp64_gpu"] = float(np.abs(u["mixed"] - u["fp64"]).sum() / np.abs(u["fp64"]).sum())
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
+    out["vs_oracle_L6"] = _mixed_vs_oracle(pkg, inputs, "euler3d", 6, t_end)
+    return out
+
+
+def _persistent(pkg, torch, p, qn, t_end: float) -> dict:
+    """The same solve in the persistent launch mode (one cooperative kernel per
+    macro step): time and kernel launches per solve, beside the default."""
+    s = pkg.Solver(p, qn)
+    s.set_launch_mode(pkg.MR_LAUNCH_PERSISTENT)
+    s.step(0.005)
+    s.reset(qn)
+    torch.cuda.synchronize()
+    l0 = s.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step(t_end)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"ms_per_solve": e0.elapsed_time(e1), "launches_per_solve": s.launch_count() - l0,
+           "launch_mode": "MR_LAUNCH_PERSISTENT (cooperative macro-step kernel, bounded grid barriers)"}
+    s.close()
+    return out
+
+
 def _cpu_baseline(seconds: float = 12.0) -> dict:
     """The FP64 oracle, as it stands, on the first fine iterations of the same
     solve (single host thread), until ~`seconds` of CPU work."""
@@ -553,7 +666,10 @@ def run_ours(args):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": (tpl * per_launch) if tpl else None,
             "kernel": "mrlt::k_stage_tile<2,2,double> (all levels, all stages)",
-            "peak_source": "measured cuBLAS DGEMM (FP64 units; nominal 1.25)",
+            "peak_source": "bench-measured cuBLAS DGEMM, 4096^3 FP64, best of 3 (MEASURED_PEAKS.json "
+                           "has no FP64 entry; nominal 1.25 TFLOP/s)",
+            "traffic_source": "profiles/stage_kernel_dram_euler2d_L10.md x leaf-stages per launch"
+                              if tpl else "no DRAM capture of this kernel version",
             "launches": prof["stage_launches"], "leaf_stages_per_launch": per_launch,
             "stage_share_of_step": stage_s / prof_solve_s,
             "timing": "CUDA events around each stage launch in one extra (profiled) solve",
@@ -617,10 +733,14 @@ def run_ours(args):
               / np.abs(u_64).reshape(u_64.shape[0], -1).sum(axis=1))
     mixed = {"ms_per_solve": min(mx_ms), "leaf_updates": mst["updates"],
              "updates_per_s": mst["updates"] / (min(mx_ms) / 1e3), "leaves_at_t_end": mst["leaves"],
-             "rel_l1_vs_fp64": [float(x) for x in rel_l1],
-             "arithmetic": "FP32 reconstruction + face fluxes; FP64 state, RK update, registers, adaptation"}
+             "rel_l1_vs_fp64_gpu": [float(x) for x in rel_l1],
+             "vs_oracle_L6": _mixed_vs_oracle(pkg, inputs, "euler2d", 6, 0.25),
+             "arithmetic": "FP32 state, exposures, reconstruction, fluxes and RK updates; "
+                           "FP64 flux registers and detail-norm threshold test"}
 
     uniform = _uniform_roofline(pkg, inputs, torch, peak)
+    precision_3d = _precision_3d(pkg, inputs, torch)
+    persistent = _persistent(pkg, torch, p, qn, args.t_end)
     paper_b2d = _paper_burgers2d(pkg, inputs, torch) if not args.no_batch else None
     paper_e2d = _paper_euler2d(pkg, inputs, torch) if not args.no_batch else None
     batched = _batched(pkg, inputs, torch) if not args.no_batch else None
@@ -635,7 +755,8 @@ def run_ours(args):
                       "leaves_at_t_end": st["leaves"], "fine_iterations": st["iters"],
                       "l2": "256 MB buffer written between steps",
                       "parallelism": f"replicas x{ws}"},
-           "clocks": clk, "gpu_launches": launches,
+           "clocks": clk, "gpu_launches": launches, "launches_per_solve": launches // max(args.steps, 1),
+           "launch_mode": "MR_LAUNCH_GRAPH (one kernel per phase, macro steps as CUDA graphs)",
            "e2e": {"value": e2e_value, "unit": UNIT,
                    "h2d_bytes_per_step": int(qn.nbytes), "d2h_bytes_per_step": int(uni_pin.nbytes)},
            "roofline": roof,
@@ -645,6 +766,8 @@ def run_ours(args):
            "lt_speedup_vs_gts": gts_s / (tmax / args.steps),
            "equal_accuracy": accuracy,
            "precision_mode": mixed,
+           "precision_mode_3d": precision_3d,
+           "persistent_launch": persistent,
            "roofline_uniform": uniform}
     if batched is not None:
         out["batched"] = batched
