@@ -96,16 +96,31 @@ typedef struct mr_config {
  * (rho, rho u_1..u_d, E), else 1).  The nodes of all levels are formed by
  * projection (Eq. 3) and, unless adapt_mode == MR_ADAPT_NEVER, the tree is
  * adapted once (Algs. 1-2).  q0 is read only during the call.
+ * Memory: each level keeps a status byte, a flag byte, a 4-byte node slot and
+ * two 4-byte list entries per cell; the values (8 fields of m variables, and
+ * for local time-stepping with reflux the flux registers, one per face) exist
+ * only for the nodes of the tree, in node arrays.  A new tree keeps room for
+ * every cell until the first macro-step boundary.  From there on (unless the
+ * full arrays take at most 32 MB, or the launch mode is MR_LAUNCH_PERSISTENT)
+ * the arrays hold 1.5 to 3 times the nodes in use: at each macro-step
+ * boundary the first remesh of the macro step is flagged and counted before
+ * its tree is installed, and the arrays are resized to fit that tree with a
+ * margin; a remesh inside a macro step that would not fit halts the
+ * solver's device work, and the host grows the arrays and resumes at that
+ * remesh (checked every 16 fine iterations), so a growing tree never fails
+ * a step while device memory lasts.  Results do not depend on the capacity.
  * Returns MR_E_INVALID for a bad configuration, MR_E_NOMEM when device memory
- * is insufficient: the exact footprint of the configuration is compared with
- * the free device memory before anything is allocated or q0 is read.  *out
- * receives the handle (NULL on failure). */
+ * is insufficient: the footprint of the full tree is compared with the free
+ * device memory before anything is allocated or q0 is read.  *out receives
+ * the handle (NULL on failure). */
 mr_status mr_create(const mr_config* cfg, const double* q0_finest, void* cuda_stream,
                     mr_solver** out);
 
 /* Re-initialise an existing solver from new finest-level data (same layout as
  * mr_create): time, counters and tree are reset exactly as mr_create would set
- * them; no device memory is allocated. */
+ * them.  Like mr_create it rebuilds the node arrays (full tree, then compact);
+ * they come from the library's memory pool, which keeps freed memory cached,
+ * so a repeated reset does not call cudaMalloc. */
 mr_status mr_reset(mr_solver* h, const double* q0_finest);
 
 /* Replace the tree by a fixed graded tree given, for every finest cell (host,
@@ -174,8 +189,10 @@ mr_status mr_set_grid_cap(mr_solver* h, int ctas);
  * the same order; the compiler may contract a different set of multiply-adds
  * in the two kernels, so they agree to FP64 round-off rather than bit for bit.
  * A barrier wait is bounded (4 s): if it gives up, the call returns
- * MR_E_TIMEOUT and the solver should be destroyed.  Only at a macro-step
- * boundary (MR_E_STATE otherwise).  The paper has no counterpart. */
+ * MR_E_TIMEOUT and the solver should be destroyed.  The persistent kernel
+ * installs trees without a host check, so switching to it gives the node
+ * arrays room for every cell (MR_E_NOMEM if that does not fit).  Only at a
+ * macro-step boundary (MR_E_STATE otherwise).  The paper has no counterpart. */
 enum { MR_LAUNCH_PERSISTENT = 0, MR_LAUNCH_GRAPH = 1 };
 mr_status mr_set_launch_mode(mr_solver* h, int mode);
 
@@ -188,6 +205,12 @@ mr_status mr_set_launch_mode(mr_solver* h, int mode);
  * device memory; synchronises cuda_stream.  The paper has no counterpart. */
 mr_status mr_selftest_grid_wait(int ctas, int missing, double limit_s, void* cuda_stream);
 
+/* Node arrays of at least `nodes` slots (the arrays are compacted and grown
+ * by the capacity rule of mr_create otherwise).  Only at a macro-step boundary
+ * (MR_E_STATE otherwise); MR_E_NOMEM if the device memory is insufficient.
+ * The paper has no counterpart. */
+mr_status mr_reserve_nodes(mr_solver* h, long long nodes);
+
 /* What mr_read returns. */
 enum {
     MR_READ_LEAF_KEYS = 0,   /* int32 [n_leaves][4]: level, i, j, k (ordered by
@@ -199,7 +222,10 @@ enum {
     MR_READ_STATS = 3,       /* double [64]: 0 t, 1 fine iterations, 2 macro steps,
                                 3 dt, 4 leaves, 5 nodes, 6 near-threshold details,
                                 7 leaf updates, 8..12 mass per variable,
-                                15 position in the macro step, 16+l leaves on level l */
+                                13 node slots (capacity), 14 device bytes held,
+                                15 position in the macro step, 16+l leaves on level l,
+                                61 remeshes that halted to grow the node arrays,
+                                62 free node slots */
     MR_READ_PROFILE = 4      /* double [64]: 0 stage-kernel launches timed since
                                 mr_profile(h,1), 1 their summed device time (ms),
                                 2..4 leaf-stages they processed for stages 1..3,
@@ -318,9 +344,12 @@ void mr_batch_destroy(mr_batch* b);
  * at macro-step boundaries, first come first served, while their
  * device footprint fits the memory budget and fewer than max_active problems
  * are in flight; a problem leaves when it reaches its end time.  The paper has
- * no counterpart.  The footprint of a configuration is known before it is
- * created (the level grids are dense): the exact bytes the solver will
- * allocate.  Results stay on the device until released. */
+ * no counterpart.  A request is admitted by its projected footprint: the
+ * per-cell arrays plus node arrays for a projected node count, which models an
+ * adapted tree as fronts of codimension one, min(all cells, 64 x 2^{(d-1) L})
+ * nodes with the compact margin of mr_create; once created, the request counts
+ * the larger of that and its actual footprint.  Results stay on the device
+ * until released. */
 typedef struct mr_server mr_server;
 
 /* mem_budget_bytes: device bytes all admitted problems may hold together;

@@ -72,6 +72,7 @@ def library() -> ctypes.CDLL:
         lib.mr_sync.argtypes = [vp]
         lib.mr_set_grid_cap.argtypes = [vp, ctypes.c_int]
         lib.mr_set_launch_mode.argtypes = [vp, ctypes.c_int]
+        lib.mr_reserve_nodes.argtypes = [vp, ll]
         lib.mr_selftest_grid_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]
         lib.mr_batch_set_grid_cap.argtypes = [vp, ctypes.c_int]
         lib.mr_server_set_grid_cap.argtypes = [vp, ctypes.c_int]
@@ -109,7 +110,7 @@ def library() -> ctypes.CDLL:
         for name in ("mr_create", "mr_reset", "mr_set_tree", "mr_adapt", "mr_step",
                      "mr_iterate", "mr_read", "mr_leaf_mass_noalloc", "mr_batch_create", "mr_create_from_state",
                      "mr_batch_step", "mr_set_async", "mr_sync", "mr_set_grid_cap", "mr_set_launch_mode",
-                     "mr_selftest_grid_wait", "mr_batch_set_grid_cap", "mr_server_set_grid_cap",
+                     "mr_selftest_grid_wait", "mr_reserve_nodes", "mr_batch_set_grid_cap", "mr_server_set_grid_cap",
                      "mr_server_create", "mr_server_submit", "mr_server_advance",
                      "mr_server_poll", "mr_server_status", "mr_server_release"):
             getattr(lib, name).restype = ctypes.c_int
@@ -307,7 +308,12 @@ class Solver:
         return {"t": s[0], "iters": int(s[1]), "macros": int(s[2]), "dt": s[3],
                 "leaves": int(s[4]), "nodes": int(s[5]), "near": int(s[6]),
                 "updates": int(s[7]), "pos": int(s[15]), "mass": s[8:8 + self.m].copy(),
+                "node_slots": int(s[13]), "device_bytes": int(s[14]), "free_slots": int(s[62]), "halts": int(s[61]),
                 "leaves_per_level": s[16:17 + L].astype(np.int64)}
+
+    def reserve_nodes(self, nodes: int):
+        """node arrays of at least `nodes` slots (at a macro-step boundary)"""
+        self._check(library().mr_reserve_nodes(self._h, int(nodes)), "reserve_nodes")
 
     def profile(self, enable: bool):
         """start / stop CUDA-event timing of the stage-kernel launches"""

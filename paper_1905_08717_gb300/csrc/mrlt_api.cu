@@ -21,12 +21,31 @@ struct mr_solver {
     mr_config cfg{};
     Launcher K;
     cudaStream_t stream = nullptr;
-    std::vector<void*> allocs;
+    std::vector<void*> allocs;      // fixed arrays (per cell, per level, scalars)
+    std::vector<void*> node_allocs; // node arrays of the current capacity
     double* d_part = nullptr;
-    double* d_T = nullptr;
-    uint8_t* d_us = nullptr;
-    int* d_keys = nullptr;
-    long long ntot = 0;
+    long long ntot = 0;             // cells over all levels
+    size_t fixed_bytes = 0;         // device bytes of the fixed arrays
+    int* h_top = nullptr;           // pinned: [0] free slots, [1] refinement flags of a head,
+                                    // [2..3] halt record (Grid::room[1..2])
+    int* d_nref = nullptr;          // device: refinement flags counted by a head
+    long long used_prev = 0;        // nodes in use at the previous capacity check
+    long long used_macro = 0;       // nodes of the tree installed at the macro step's start
+    long long grow_macro = 0;       // largest growth past used_macro seen in this macro step
+    // head of a macro step: iteration 0 up to the flags of its new tree (and
+    // their count), run before the capacity check at the boundary
+    bool head_pending = false;      // enqueued, its count not yet applied
+    bool head_done = false;         // applied: iteration 0 continues with the tree's installation
+    cudaGraphExec_t head_exec = nullptr;
+    long long head_launches = 0;
+    // a remesh that did not fit halted the device work (see halted()): the
+    // host resumes at the halted iteration (resume: with the installation of
+    // its tree) and launches `redo` iterations again without counting them
+    bool resume = false;
+    long long redo = 0;
+    bool unchecked = false;         // iterations launched since the last check point
+    long long halts = 0;            // halts recovered (statistics)
+    long long reserved = 0;         // mr_reserve_nodes: capacity floor
     double t = 0.0, dt = 0.0;
     long long iters = 0, macros = 0, pos = 0, stage_launches = 0;
     bool reg = false;
@@ -47,6 +66,10 @@ struct mr_solver {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t macro_exec = nullptr;
     long long macro_launches = 0, macro_stage_launches = 0;
+    // pieces of a macro step between capacity checks (compact node arrays):
+    // graphs of kPiece iterations, one per position in the macro step
+    std::vector<cudaGraphExec_t> piece_exec;
+    std::vector<long long> piece_launches, piece_stage_launches;
     bool graph_off = false; // capture failed once, or disabled by the caller
     // batched use: the macro-step finiteness check copies the device error
     // bits here (pinned host memory) instead of synchronising
@@ -178,6 +201,260 @@ mr_status dev_alloc(mr_solver* h, T** p, size_t count)
     return MR_OK;
 }
 
+// ---------------------------------------------------------------- node storage
+// Node values live in arrays of `cap` slots (see mrlt_impl.cuh).  A new tree
+// (creation, reset, a full adaptation, an installed tree) gets room for every
+// cell of every level.  A solver whose full arrays cost at most kDenseBytes
+// keeps them, and so does the persistent launch mode; any other is resized
+// at macro-step boundaries, where the size of the next tree is known
+// exactly: the first fine iteration of a macro step, which holds its only
+// full remesh, is split after the adaptation has flagged the new tree (the
+// head of the macro step).  The flags are counted (every refined cell owns
+// 2^d children), the count is read back together with the CFL speed, and
+// the arrays are resized before the tree is installed.  With need = max(nodes
+// in use, nodes of the next tree) and margin = max(the largest growth seen
+// within the last macro step, a quarter of need, kMinSlots), arrays with
+// fewer than need + margin or more than need + 4 margin slots are set to
+// need + 2 margin.  Inside a macro step (adaptation at every fine iteration,
+// on the levels that are active) every remesh first checks on the device
+// that its tree fits, and halts the solver's device work if it does not
+// (k_room).  The host reads the free-slot count and the halt record at check
+// points every kPiece fine iterations (a macro step runs in pieces of kPiece
+// iterations, each its own CUDA graph) and at the end of a macro step: after
+// a halt it grows the arrays to the flagged tree plus two margins of a
+// quarter of it and resumes at the halted remesh; otherwise, with margin =
+// max(2 x the nodes added since the last check, a quarter of the nodes in
+// use, kMinSlots), fewer than margin free slots grow the arrays to used + 2
+// margin.  Reservations made with mr_reserve_nodes are a floor.
+constexpr long long kMinSlots = 4096;
+constexpr long long kPiece = 16;
+constexpr size_t kDenseBytes = 32u << 20;
+
+size_t per_node_bytes(const Grid& g, bool reg)
+{
+    const size_t esz = g.prec ? sizeof(float) : sizeof(double);
+    return NFIELD * g.m * esz + (reg ? (size_t)g.nf * g.m * sizeof(double) : 0) + sizeof(int);
+}
+
+// new node arrays of cap slots into g (fields, registers, free stack);
+// the previous pointers are not freed here
+mr_status alloc_nodes(mr_solver* h, Grid& g, long long cap, std::vector<void*>& out)
+{
+    cudaMemPool_t pool = device_pool();
+    auto take = [&](void** p, size_t bytes) -> bool {
+        *p = nullptr;
+        if (!pool || cudaMallocFromPoolAsync(p, bytes, pool, h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        out.push_back(*p);
+        return true;
+    };
+    const size_t esz = g.prec ? sizeof(float) : sizeof(double);
+    bool ok = true;
+    for (int f = 0; f < NFIELD && ok; ++f) ok = take(&g.f[f], (size_t)cap * g.m * esz);
+    if (ok && h->reg) {
+        ok = take((void**)&g.rg, (size_t)cap * g.nf * g.m * sizeof(double));
+    } else if (ok) {
+        g.rg = nullptr;
+    }
+    if (ok) ok = take((void**)&g.fstack, (size_t)cap * sizeof(int));
+    if (!ok) {
+        h->err = "device allocation of node arrays failed";
+        return MR_E_NOMEM;
+    }
+    g.cap = cap;
+    return MR_OK;
+}
+
+void drop_graphs(mr_solver* h);
+
+void free_allocs(mr_solver* h, std::vector<void*>& v)
+{
+    for (void* p : v) cudaFreeAsync(p, h->stream);
+    v.clear();
+}
+
+// Replace the node arrays by arrays of newcap slots.  keep: copy the live
+// nodes (compacted into slots 1..used, in level and list order); otherwise
+// the arrays are fresh (the caller initialises them).  A captured macro step
+// holds the old pointers, so it is dropped.
+mr_status set_capacity(mr_solver* h, long long newcap, bool keep)
+{
+    Grid& g = h->K.g;
+    if (newcap > h->ntot + 1) newcap = h->ntot + 1;
+    if (newcap == g.cap) return MR_OK;
+    int cnt[2 * (LMAX + 1)] = {};
+    long long used = 0;
+    if (keep) {
+        MR_CK(cudaMemcpyAsync(cnt, g.counts, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
+        MR_CK(cudaStreamSynchronize(h->stream));
+        for (int l = g.lb; l <= g.L; ++l) used += cnt[l] + cnt[LMAX + 1 + l];
+        if (used + 1 > newcap) newcap = used + 1;
+    }
+    if (h->macro_exec || h->head_exec || !h->piece_exec.empty()) { // captured with the old arrays
+        MR_CK(cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+    }
+    const Grid from = g;
+    std::vector<void*> fresh;
+    MR_TRY(alloc_nodes(h, g, newcap, fresh));
+    if (keep) h->K.renumber(from, cnt, used);
+    free_allocs(h, h->node_allocs);
+    h->node_allocs.swap(fresh);
+    h->bytes = h->fixed_bytes + (size_t)newcap * per_node_bytes(g, h->reg);
+    MR_CK(cudaGetLastError());
+    return MR_OK;
+}
+
+// node arrays with a slot for every cell (no resizing needed)
+bool dense_capacity(const mr_solver* h) { return h->K.g.cap >= h->ntot + 1; }
+
+// room for every cell is cheap enough to keep
+bool small_problem(const mr_solver* h)
+{
+    return (size_t)(h->ntot + 1) * per_node_bytes(h->K.g, h->reg) <= kDenseBytes;
+}
+
+// the macro step's head is split off iteration 0 (see the capacity rule)
+bool split_head(const mr_solver* h)
+{
+    return h->cfg.adapt_mode != MR_ADAPT_NEVER && !small_problem(h) && h->launch_mode == MR_LAUNCH_GRAPH;
+}
+
+// remeshes inside macro steps check that their trees fit (and halt if not)
+bool can_halt(const mr_solver* h)
+{
+    return split_head(h) && h->cfg.adapt_mode == MR_ADAPT_EVERY;
+}
+
+// The capacity rule at a check point, with the free-slot count `top` read
+// back: a macro-step boundary (next = nodes of the tree its head flagged, or
+// -1 when the tree does not change there) or a check between pieces.
+mr_status adjust_capacity(mr_solver* h, int top, bool boundary, long long next = -1)
+{
+    if ((small_problem(h) || h->launch_mode == MR_LAUNCH_PERSISTENT) && dense_capacity(h)) return MR_OK;
+    const long long cap = h->K.g.cap, used = cap - 1 - top;
+    auto clamp = [&](long long t) {
+        if (t < h->reserved + 1) t = h->reserved + 1;
+        return t > h->ntot + 1 ? h->ntot + 1 : t;
+    };
+    auto at_least = [](long long a, long long b) { return a > b ? a : b; };
+    if (used - h->used_macro > h->grow_macro) h->grow_macro = used - h->used_macro;
+    if (boundary) {
+        const long long need = at_least(used, next);
+        const long long margin = at_least(at_least(h->grow_macro, need / 4), kMinSlots);
+        const long long target = clamp(need + 2 * margin + 1);
+        h->used_prev = h->used_macro = next >= 0 ? next : used;
+        h->grow_macro = 0;
+        if (cap - 1 < need + margin || cap - 1 > need + 4 * margin) return set_capacity(h, target, true);
+        return MR_OK;
+    }
+    if (dense_capacity(h)) return MR_OK;
+    const long long added = used > h->used_prev ? used - h->used_prev : 0;
+    h->used_prev = used;
+    const long long margin = at_least(at_least(2 * added, used / 4), kMinSlots);
+    const long long target = clamp(used + 2 * margin + 1);
+    if (top < margin && cap < target) return set_capacity(h, target, true);
+    return MR_OK;
+}
+
+// nodes in use (a synchronising read of the lists' counts)
+mr_status count_nodes(mr_solver* h, long long* used)
+{
+    int cnt[2 * (LMAX + 1)] = {};
+    MR_CK(cudaMemcpyAsync(cnt, h->K.g.counts, sizeof cnt, cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaStreamSynchronize(h->stream));
+    *used = 0;
+    for (int l = h->K.g.lb; l <= h->K.g.L; ++l) *used += cnt[l] + cnt[LMAX + 1 + l];
+    return MR_OK;
+}
+
+// end of a call that built a new tree (held in arrays with room for every
+// cell until the next macro-step boundary)
+mr_status fit_new_tree(mr_solver* h)
+{
+    long long used = 0;
+    MR_TRY(count_nodes(h, &used));
+    h->used_prev = h->used_macro = used;
+    h->grow_macro = 0;
+    h->head_pending = h->head_done = false;
+    return MR_OK;
+}
+
+// A check point inside a macro step: the free-slot count and the halt
+// record read back (synchronising).  After a halt at iteration p the arrays
+// grow to hold the flagged tree and two margins of a quarter of it, the
+// halt is cleared and the position rewinds to p: the caller resumes with the
+// installation of p's tree (its flags are intact: nothing ran after them)
+// and launches the iterations after p again.  Otherwise the capacity rule.
+mr_status check_point(mr_solver* h, bool* rewound)
+{
+    Grid& g = h->K.g;
+    *rewound = false;
+    MR_CK(cudaMemcpyAsync(h->h_top, g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaMemcpyAsync(h->h_top + 2, g.room + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaStreamSynchronize(h->stream));
+    if (!h->h_top[2]) return adjust_capacity(h, h->h_top[0], false);
+    const long long p = h->h_top[2] - 1, tree = h->h_top[3];
+    if (p < 1 || p >= h->pos) {
+        h->err = "halt record out of range";
+        return MR_E_STATE;
+    }
+    MR_CK(cudaMemsetAsync(g.room, 0, 4 * sizeof(int), h->stream));
+    h->h_top[2] = h->h_top[3] = 0;
+    const long long used = g.cap - 1 - h->h_top[0];
+    const long long need = tree > used ? tree : used;
+    long long margin = need / 4;
+    if (margin < kMinSlots) margin = kMinSlots;
+    long long target = need + 2 * margin + 1;
+    if (target < h->reserved + 1) target = h->reserved + 1;
+    MR_TRY(set_capacity(h, target, true));
+    h->used_prev = need;
+    if (need - h->used_macro > h->grow_macro) h->grow_macro = need - h->used_macro;
+    h->redo += h->pos - p;
+    h->pos = p;
+    h->resume = true;
+    ++h->halts;
+    *rewound = true;
+    return MR_OK;
+}
+
+// fine iterations between capacity checks inside a macro step (only
+// adaptation at every fine iteration changes the tree there)
+long long piece_len(const mr_solver* h, long long nit)
+{
+    if (dense_capacity(h) || nit <= kPiece || h->cfg.adapt_mode != MR_ADAPT_EVERY) return nit;
+    return kPiece;
+}
+
+void drop_graphs(mr_solver* h)
+{
+    if (h->macro_exec) cudaGraphExecDestroy(h->macro_exec);
+    h->macro_exec = nullptr;
+    if (h->head_exec) cudaGraphExecDestroy(h->head_exec);
+    h->head_exec = nullptr;
+    for (cudaGraphExec_t e : h->piece_exec)
+        if (e) cudaGraphExecDestroy(e);
+    h->piece_exec.clear();
+    h->piece_launches.clear();
+    h->piece_stage_launches.clear();
+}
+
+// transient device scratch from the pool, released in stream order
+template <class T>
+mr_status scratch(mr_solver* h, T** p, size_t count)
+{
+    *p = nullptr;
+    cudaMemPool_t pool = device_pool();
+    if (!pool || cudaMallocFromPoolAsync((void**)p, count * sizeof(T) + 16, pool, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "device allocation of scratch memory failed";
+        return MR_E_NOMEM;
+    }
+    return MR_OK;
+}
+
 int level_min(const mr_solver* h, long long n)
 {
     const Grid& g = h->K.g;
@@ -246,37 +523,55 @@ mr_status sync_check(mr_solver* h)
                  (e & ERR_TIMEOUT) ? " (a grid barrier wait gave up)" : "");
         h->err = buf;
         if (e & ERR_TIMEOUT) return MR_E_TIMEOUT;
+        if (e & ERR_CAPACITY) {
+            h->err += " (node capacity exhausted within a macro step: the tree more than doubled; "
+                      "reserve more nodes with mr_reserve_nodes)";
+            return MR_E_NOMEM;
+        }
         return (e & ERR_NONFINITE) ? MR_E_NUMERIC : MR_E_STATE;
     }
     return MR_OK;
 }
 
 // Algs. 1-2 restricted to levels >= la (full adaptation for la = min_level)
-mr_status adapt(mr_solver* h, int la)
+// part 1: details, thresholds and closure (the new tree in the flags); part
+// 2: the tree installed (slots released and taken), lists, projections; 0:
+// both.  A caller may check the node capacity between the parts.
+mr_status adapt(mr_solver* h, int la, int part = 0, long long it = 0)
 {
     Grid& g = h->K.g;
     if (la >= g.L) return MR_OK;
-    if (la == g.lb) {
-        h->K.scale_init();
-        for (int l = g.lb; l <= g.L; ++l) h->K.scale(l);
+    if (part != 2) {
+        if (la == g.lb) {
+            h->K.scale_init();
+            for (int l = g.lb; l <= g.L; ++l) h->K.scale(l);
+        }
+        h->K.clear_flags(g.off[la], h->ntot);
+        h->K.mark_refinements(la);
+        if (part == 0 && can_halt(h)) h->K.check_room(la, it);
     }
-    MR_CK(cudaMemsetAsync(g.flag + g.off[la], 0, (size_t)(h->ntot - g.off[la]), h->stream));
-    h->K.mark_refinements(la);
-    h->K.apply_tree(la);
-    h->K.compact(la, g.L);
-    for (int l = g.L - 1; l >= la; --l) h->K.project(l, PM_Q0);
+    if (part != 1) {
+        h->K.apply_tree(la);
+        h->K.compact(la, g.L);
+        for (int l = g.L - 1; l >= la; --l) h->K.project(l, PM_Q0);
+    }
     return MR_OK;
 }
 
 // one iteration n (0-based in the macro step) of Alg. 3
-mr_status lt_iteration(mr_solver* h, long long n, long long nit)
+// part 1 ends inside the adaptation, before the new tree is installed;
+// part 2 continues from there (see adapt); 0: the whole iteration
+mr_status lt_iteration(mr_solver* h, long long n, long long nit, int part = 0)
 {
     Grid& g = h->K.g;
     const int L = g.L, lb = g.lb, lmin = level_min(h, n);
-    h->K.leaf_copy(lmin, L, F_QE, F_Q0);
-    for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_Q0);
+    if (part != 2) {
+        h->K.leaf_copy(lmin, L, F_QE, F_Q0);
+        for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_Q0);
+    }
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
-        MR_TRY(adapt(h, lmin));
+        MR_TRY(adapt(h, lmin, part, n));
+    if (part == 1) return MR_OK;
     if (lmin > lb) h->K.project(lmin - 1, PM_MID);
     stage(h, lmin, L, 1, lmin); // first stage: all active levels at once
     for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF2);
@@ -299,14 +594,17 @@ mr_status lt_iteration(mr_solver* h, long long n, long long nit)
 }
 
 // global time step MR (MR/RK2, MR/RK3)
-mr_status gts_iteration(mr_solver* h, long long n)
+mr_status gts_iteration(mr_solver* h, long long n, int part = 0)
 {
     Grid& g = h->K.g;
     const int L = g.L, lb = g.lb;
-    h->K.leaf_copy(lb, L, F_QE, F_Q0);
-    for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
+    if (part != 2) {
+        h->K.leaf_copy(lb, L, F_QE, F_Q0);
+        for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
+    }
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
-        MR_TRY(adapt(h, lb));
+        MR_TRY(adapt(h, lb, part, n));
+    if (part == 1) return MR_OK;
     stage(h, lb, L, 1, lb); // every level at the same instant: one launch per stage
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q1);
     stage(h, lb, L, 2, lb);
@@ -327,18 +625,23 @@ mr_status finite_check(mr_solver* h)
     return sync_check(h);
 }
 
-mr_status iteration(mr_solver* h, long long n, long long nit)
+mr_status iteration(mr_solver* h, long long n, long long nit, int part = 0)
 {
-    return h->K.g.gts ? gts_iteration(h, n) : lt_iteration(h, n, nit);
+    return h->K.g.gts ? gts_iteration(h, n, part) : lt_iteration(h, n, nit, part);
 }
 
-// Capture the nit fine iterations of one macro step as a CUDA graph (stream
-// capture on the internal stream).  Every launch of a macro step is fixed by
-// the layout, the level schedule l_min(n) and the configuration; the fine
-// step is read from g.dtp, so one graph serves every macro step.  Returns
-// false (and leaves nothing captured) when capture is not possible; the
-// caller then launches directly.
-bool capture_macro(mr_solver* h, long long nit)
+// the part of iteration n that a macro step runs after its head (see the
+// capacity rule): the rest of iteration 0 when the head was split off
+int part_of(const mr_solver* h, long long n) { return n == 0 && split_head(h) ? 2 : 0; }
+
+// Capture what `body` enqueues as a CUDA graph (stream capture on the
+// internal stream).  Every launch of a macro step is fixed by the layout,
+// the level schedule l_min(n) and the configuration; the fine step is read
+// from g.dtp, so one graph serves every macro step.  Returns false (and
+// leaves nothing captured) when capture is not possible; the caller then
+// launches directly.
+template <class Body>
+bool capture(mr_solver* h, Body body, cudaGraphExec_t* exec, long long* launches, long long* stage_launches)
 {
     if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -347,24 +650,90 @@ bool capture_macro(mr_solver* h, long long nit)
     // stage-kernel attributes and occupancy are set up before capture begins
     if (launch_stage(h->K.g, h->stream, 1, 0, 1, 0, 0.0, 0) < 0) return false;
     cudaStream_t user = h->stream;
-    const long long n0 = h->K.n, s0 = h->stage_launches;
+    const long long k0 = h->K.n, s0 = h->stage_launches;
     h->stream = h->K.st = h->cap_stream;
     bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    mr_status r = MR_OK;
-    for (long long i = 0; ok && i < nit && r == MR_OK; ++i) r = iteration(h, i, nit);
+    const mr_status r = ok ? body() : MR_OK;
     cudaGraph_t graph = nullptr;
     if (ok) ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess && r == MR_OK && !h->launch_failed;
     h->stream = h->K.st = user;
     h->launch_failed = false;
-    if (ok) ok = cudaGraphInstantiate(&h->macro_exec, graph, 0) == cudaSuccess;
+    *exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(exec, graph, 0) == cudaSuccess;
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError(); // clear a capture error so that the direct path starts clean
-    h->macro_launches = h->K.n - n0;
-    h->macro_stage_launches = h->stage_launches - s0;
-    h->K.n = n0;
+    *launches = h->K.n - k0;
+    if (stage_launches) *stage_launches = h->stage_launches - s0;
+    h->K.n = k0;
     h->stage_launches = s0;
-    if (!ok) h->macro_exec = nullptr;
+    if (!ok) *exec = nullptr;
     return ok;
+}
+
+// fine iterations [n0, n0 + cnt) of a macro step (iteration 0 from its head on)
+bool capture_iters(mr_solver* h, long long n0, long long cnt, long long nit, cudaGraphExec_t* exec,
+                   long long* launches, long long* stage_launches)
+{
+    auto body = [&]() -> mr_status {
+        for (long long i = n0; i < n0 + cnt; ++i) MR_TRY(iteration(h, i, nit, part_of(h, i)));
+        return MR_OK;
+    };
+    return capture(h, body, exec, launches, stage_launches);
+}
+
+bool capture_macro(mr_solver* h, long long nit)
+{
+    return capture_iters(h, 0, nit, nit, &h->macro_exec, &h->macro_launches, &h->macro_stage_launches);
+}
+
+// The head of the next macro step (iteration 0 up to the flags of the new
+// tree, and their count) enqueued, the count and the free-slot count on
+// their way to h_top; head_finish applies them once the stream has passed.
+mr_status head_enqueue(mr_solver* h)
+{
+    if (!split_head(h) || h->head_done || h->head_pending) return MR_OK;
+    const long long nit = 1LL << (h->K.g.L - h->K.g.lb);
+    auto body = [&]() -> mr_status {
+        MR_TRY(iteration(h, 0, nit, 1));
+        h->K.count_refined(h->K.g.lb, h->d_nref);
+        return MR_OK;
+    };
+    bool graphed = false;
+    if (!h->prof && !h->graph_off) {
+        if (h->head_exec || capture(h, body, &h->head_exec, &h->head_launches, nullptr)) {
+            MR_CK(cudaGraphLaunch(h->head_exec, h->stream));
+            h->K.n += h->head_launches;
+            graphed = true;
+        } else {
+            h->graph_off = true;
+        }
+    }
+    if (!graphed) MR_TRY(body());
+    MR_CK(cudaMemcpyAsync(h->h_top + 1, h->d_nref, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaMemcpyAsync(h->h_top, h->K.g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    h->head_pending = true;
+    return MR_OK;
+}
+
+// the capacity rule at a macro-step boundary, once h_top holds what the
+// head (if any) and the free-slot read enqueued before it
+mr_status head_finish(mr_solver* h)
+{
+    if (!h->head_pending) return adjust_capacity(h, h->h_top[0], true);
+    h->head_pending = false;
+    h->head_done = true;
+    const Grid& g = h->K.g;
+    const long long next = g.N[g.lb] + ((long long)h->h_top[1] << g.d);
+    return adjust_capacity(h, h->h_top[0], true, next);
+}
+
+// head and capacity rule of a macro-step boundary, synchronously
+mr_status boundary_check(mr_solver* h)
+{
+    MR_TRY(head_enqueue(h));
+    MR_CK(cudaMemcpyAsync(h->h_top, h->K.g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MR_TRY(sync_check(h));
+    return head_finish(h);
 }
 
 // Graphs are used for whole macro steps with profiling off, up to 1024 fine
@@ -439,19 +808,34 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
         return MR_E_STATE;
     }
     h->dt = dt;
-    long long i = 0;
-    while (i < n) {
-        if (h->pos == 0) h->K.set_dt(dt);
-        if (h->launch_mode == MR_LAUNCH_PERSISTENT) {
-            long long chunk = n - i < nit - h->pos ? n - i : nit - h->pos;
-            if (h->prof && chunk > kProfIters) chunk = kProfIters;
-            MR_TRY(run_persistent(h, chunk, nit));
-            h->iters += chunk;
-            h->pos += chunk;
-            i += chunk;
-            if (h->pos == nit) {
-                h->pos = 0;
-                ++h->macros;
+    long long i = 0; // new iterations launched by this call
+    // k iterations launched from h->pos (the first ones again after a halt)
+    auto advance = [&](long long k) {
+        const long long fresh = k > h->redo ? k - h->redo : 0;
+        h->redo = h->redo > k ? h->redo - k : 0;
+        h->iters += fresh;
+        i += fresh;
+        h->pos += k;
+        h->head_done = h->resume = false;
+        h->unchecked = can_halt(h) && !dense_capacity(h);
+    };
+    for (;;) {
+        const bool done = i >= n && h->redo == 0;
+        // check points: every kPiece fine iterations, the end of a macro
+        // step and the end of this call (compact arrays, remeshes at every
+        // fine iteration)
+        if (h->unchecked && (h->pos % kPiece == 0 || h->pos == nit || done)) {
+            h->unchecked = false;
+            bool rewound = false;
+            MR_TRY(check_point(h, &rewound));
+            if (rewound) continue;
+        }
+        if (h->pos == nit) { // every iteration of the macro step launched
+            h->pos = 0;
+            ++h->macros;
+            if (h->launch_mode != MR_LAUNCH_PERSISTENT) {
+                MR_TRY(finite_check(h));
+            } else {
                 h->wmax_valid = true; // the kernel ended with the CFL reduction
                 if (h->async_err) {
                     MR_CK(cudaMemcpyAsync(h->async_err, h->K.g.err, sizeof(int), cudaMemcpyDeviceToHost,
@@ -460,34 +844,60 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
                     MR_TRY(sync_check(h));
                 }
             }
+        }
+        if (i >= n && h->redo == 0) break;
+        if (h->pos == 0) {
+            if (split_head(h) && !h->head_done) MR_TRY(boundary_check(h));
+            h->K.set_dt(dt);
+        }
+        if (h->resume) { // the halted iteration from its tree's installation on
+            MR_TRY(iteration(h, h->pos, nit, 2));
+            h->wmax_valid = false;
+            advance(1);
+            continue;
+        }
+        const long long piece = piece_len(h, nit);
+        const long long left = n - i + h->redo; // iterations still to launch
+        if (h->launch_mode == MR_LAUNCH_PERSISTENT) {
+            long long chunk = left < nit - h->pos ? left : nit - h->pos;
+            if (h->prof && chunk > kProfIters) chunk = kProfIters;
+            MR_TRY(run_persistent(h, chunk, nit));
+            advance(chunk);
             continue;
         }
         h->wmax_valid = false;
-        bool graph = h->pos == 0 && n - i >= nit && !h->prof && !h->graph_off && nit <= kMaxGraphIters;
-        if (graph && !h->macro_exec && !capture_macro(h, nit)) {
-            h->graph_off = true; // launch directly from now on
-            graph = false;
-        }
-        if (graph) {
+        const bool can_graph = !h->prof && !h->graph_off && nit <= kMaxGraphIters;
+        if (can_graph && piece == nit && h->pos == 0 && left >= nit) { // a whole macro step
+            if (!h->macro_exec && !capture_macro(h, nit)) {
+                h->graph_off = true; // launch directly from now on
+                continue;
+            }
             MR_CK(cudaGraphLaunch(h->macro_exec, h->stream));
             h->K.n += h->macro_launches;
             h->stage_launches += h->macro_stage_launches;
-            h->iters += nit;
-            i += nit;
-            h->pos = 0;
-            ++h->macros;
-            MR_TRY(finite_check(h));
+            advance(nit);
             continue;
         }
-        MR_TRY(iteration(h, h->pos, nit));
-        ++h->iters;
-        ++h->pos;
-        ++i;
-        if (h->pos == nit) {
-            h->pos = 0;
-            ++h->macros;
-            MR_TRY(finite_check(h));
+        if (can_graph && piece < nit && h->pos % piece == 0 && left >= piece) { // a piece of one
+            const size_t k = (size_t)(h->pos / piece);
+            if (h->piece_exec.size() != (size_t)(nit / piece)) {
+                h->piece_exec.assign((size_t)(nit / piece), nullptr);
+                h->piece_launches.assign((size_t)(nit / piece), 0);
+                h->piece_stage_launches.assign((size_t)(nit / piece), 0);
+            }
+            if (!h->piece_exec[k] && !capture_iters(h, h->pos, piece, nit, &h->piece_exec[k], &h->piece_launches[k],
+                                                    &h->piece_stage_launches[k])) {
+                h->graph_off = true;
+                continue;
+            }
+            MR_CK(cudaGraphLaunch(h->piece_exec[k], h->stream));
+            h->K.n += h->piece_launches[k];
+            h->stage_launches += h->piece_stage_launches[k];
+            advance(piece);
+            continue;
         }
+        MR_TRY(iteration(h, h->pos, nit, part_of(h, h->pos)));
+        advance(1);
     }
     return MR_OK;
 }
@@ -499,6 +909,8 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
 mr_status cfl_enqueue(mr_solver* h, unsigned long long* bits)
 {
     Grid& g = h->K.g;
+    // free node slots, for the capacity rule at this macro-step boundary
+    MR_CK(cudaMemcpyAsync(h->h_top, g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     if (h->wmax_valid) { // computed at the end of the macro-step kernel that led to this state
         MR_CK(cudaMemcpyAsync(bits, g.wmax, sizeof *bits, cudaMemcpyDeviceToHost, h->stream));
         return MR_OK;
@@ -542,28 +954,25 @@ mr_status init_state(mr_solver* h, const double* q0)
 {
     Grid& g = h->K.g;
     const int m = g.m;
-    const size_t nd = (size_t)h->ntot * m;
+    // the full tree: every cell of every level a node, then adapted
+    MR_TRY(set_capacity(h, h->ntot + 1, false));
     const size_t esz = g.prec ? sizeof(float) : sizeof(double); // field element
-    for (int f = 0; f < NFIELD; ++f) MR_CK(cudaMemsetAsync(g.f[f], 0, nd * esz, h->stream));
-    if (g.rc) {
-        MR_CK(cudaMemsetAsync(g.rc, 0, nd * g.nf * sizeof(double), h->stream));
-        MR_CK(cudaMemsetAsync(g.rf, 0, nd * g.nf * sizeof(double), h->stream));
-    }
+    for (int f = 0; f < NFIELD; ++f) MR_CK(cudaMemsetAsync(g.f[f], 0, (size_t)g.cap * m * esz, h->stream));
+    if (g.rg) MR_CK(cudaMemsetAsync(g.rg, 0, (size_t)g.cap * g.nf * m * sizeof(double), h->stream));
     MR_CK(cudaMemsetAsync(g.flag, 0, h->ntot, h->stream));
     MR_CK(cudaMemsetAsync(g.counts, 0, 3 * (LMAX + 1) * sizeof(int), h->stream));
     MR_CK(cudaMemsetAsync(g.err, 0, sizeof(int), h->stream));
+    MR_CK(cudaMemsetAsync(g.room, 0, 4 * sizeof(int), h->stream));
     MR_CK(cudaMemsetAsync(g.near, 0, sizeof(unsigned long long), h->stream));
     MR_CK(cudaMemsetAsync(g.updates, 0, sizeof(unsigned long long), h->stream));
-    if (g.prec) { // FP32 state: through the double scratch, rounded on the device
-        MR_CK(cudaMemcpyAsync(h->d_T, q0, (size_t)g.N[g.L] * m * sizeof(double), cudaMemcpyHostToDevice,
-                              h->stream));
-        h->K.store_finest(h->d_T);
-    } else {
-        MR_CK(cudaMemcpyAsync(static_cast<double*>(g.f[F_Q0]) + g.off[g.L] * m, q0,
-                              (size_t)g.N[g.L] * m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    }
     for (int l = g.lb; l <= g.L; ++l)
         MR_CK(cudaMemsetAsync(g.st + g.off[l], l < g.L ? 2 : 1, (size_t)g.N[l], h->stream));
+    h->K.slots_full(h->ntot);
+    double* d_q = nullptr; // finest data through a transient double buffer, stored in the fields' type
+    MR_TRY(scratch(h, &d_q, (size_t)g.N[g.L] * m));
+    MR_CK(cudaMemcpyAsync(d_q, q0, (size_t)g.N[g.L] * m * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->K.store_finest(d_q);
+    MR_CK(cudaFreeAsync(d_q, h->stream));
     h->K.compact(g.lb, g.L);
     for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
     if (h->cfg.adapt_mode != MR_ADAPT_NEVER) MR_TRY(adapt(h, g.lb));
@@ -571,7 +980,8 @@ mr_status init_state(mr_solver* h, const double* q0)
     h->t = h->dt = 0.0;
     h->iters = h->macros = h->pos = 0;
     h->wmax_valid = false;
-    return sync_check(h);
+    MR_TRY(sync_check(h));
+    return fit_new_tree(h);
 }
 
 } // namespace
@@ -632,15 +1042,8 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     };
     A(dev_alloc(h, &g.st, off));
     A(dev_alloc(h, &g.flag, off));
-    for (int f = 0; f < NFIELD; ++f) { // double, or float in the mixed mode
-        unsigned char* p = nullptr;
-        A(dev_alloc(h, &p, nd * (g.prec ? sizeof(float) : sizeof(double))));
-        g.f[f] = p;
-    }
-    if (h->reg) {
-        A(dev_alloc(h, &g.rc, nd * g.nf));
-        A(dev_alloc(h, &g.rf, nd * g.nf));
-    }
+    A(dev_alloc(h, &g.slot, off));
+    A(dev_alloc(h, &g.ftop, 2));
     A(dev_alloc(h, &g.leaves, off));
     A(dev_alloc(h, &g.inner, off));
     A(dev_alloc(h, &g.counts, 3 * (LMAX + 1)));
@@ -648,12 +1051,14 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     A(dev_alloc(h, &g.tlist, (size_t)toff));
     A(dev_alloc(h, &g.scale_bits, MMAX));
     A(dev_alloc(h, &g.dtp, 1));
+    A(dev_alloc(h, &g.room, 4));
     A(dev_alloc(h, &g.err, 1));
     A(dev_alloc(h, &g.near, 1));
     A(dev_alloc(h, &g.wmax, 1));
     A(dev_alloc(h, &g.updates, 1));
     A(dev_alloc(h, &g.work, (LMAX + 1) * 4));
     A(dev_alloc(h, &h->d_bar, 2));
+    A(dev_alloc(h, &h->d_nref, 1));
     if (r == MR_OK && !h->dry &&
         cudaMemsetAsync(g.work, 0, (LMAX + 1) * 4 * sizeof(unsigned long long), h->stream) != cudaSuccess)
         r = MR_E_CUDA; // cumulative counters: never cleared by mr_reset
@@ -661,9 +1066,24 @@ mr_status layout_alloc(mr_solver* h, const mr_config* cfg)
     for (int l = g.lb; l <= g.L; ++l) nblk += (g.N[l] + NTHREADS - 1) / NTHREADS;
     A(dev_alloc(h, &h->K.bc, 2 * nblk));
     A(dev_alloc(h, &h->d_part, (size_t)(LMAX + 1) * MASS_BLOCKS * g.m));
-    A(dev_alloc(h, &h->d_T, nd));
-    A(dev_alloc(h, &h->d_us, off));
-    A(dev_alloc(h, &h->d_keys, off * 4));
+    (void)nd;
+    h->fixed_bytes = h->bytes;
+    // node arrays: the full tree of a new solver (every cell a node) plus the sink
+    if (h->dry) {
+        h->bytes += (size_t)(off + 1) * per_node_bytes(g, h->reg);
+        g.cap = off + 1;
+    } else if (r == MR_OK) {
+        r = alloc_nodes(h, g, off + 1, h->node_allocs);
+        h->bytes = h->fixed_bytes + (size_t)(off + 1) * per_node_bytes(g, h->reg);
+    }
+    if (r == MR_OK && !h->dry && !h->h_top) {
+        if (cudaMallocHost((void**)&h->h_top, 4 * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            r = MR_E_NOMEM;
+        } else {
+            memset(h->h_top, 0, 4 * sizeof(int));
+        }
+    }
     return r;
 }
 
@@ -789,11 +1209,13 @@ mr_status mr_set_tree(mr_solver* h, const unsigned char* lev)
         for (long long id = 0; id < g.N[l]; ++id)
             if (R[l][id]) fl[g.off[l] + id] = FL_REF;
     MR_CK(cudaMemcpyAsync(g.flag, fl.data(), fl.size(), cudaMemcpyHostToDevice, h->stream));
+    MR_TRY(set_capacity(h, h->ntot + 1, true)); // room for any tree, compacted at the end
     h->K.apply_tree(lb);
     h->K.compact(lb, L);
     for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
     h->K.leaf_copy(lb, L, F_Q0, F_QE);
-    return sync_check(h);
+    MR_TRY(sync_check(h));
+    return fit_new_tree(h);
 }
 
 mr_status mr_create_from_state(const mr_config* cfg, long long n_leaves, const int* keys, const double* values,
@@ -839,14 +1261,18 @@ mr_status mr_create_from_state(const mr_config* cfg, long long n_leaves, const i
     h->cfg = *cfg;
     mr_status r = mr_set_tree(h, map.data());
     Grid& g = h->K.g;
-    if (r == MR_OK && cudaMemcpyAsync(h->d_keys, keys, sizeof(int) * 4 * (size_t)n_leaves, cudaMemcpyHostToDevice,
+    int* d_keys = nullptr;
+    double* d_vals = nullptr;
+    if (r == MR_OK) r = scratch(h, &d_keys, (size_t)4 * n_leaves);
+    if (r == MR_OK) r = scratch(h, &d_vals, (size_t)m * n_leaves);
+    if (r == MR_OK && cudaMemcpyAsync(d_keys, keys, sizeof(int) * 4 * (size_t)n_leaves, cudaMemcpyHostToDevice,
                                       h->stream) != cudaSuccess)
         r = MR_E_CUDA;
-    if (r == MR_OK && cudaMemcpyAsync(h->d_T, values, sizeof(double) * (size_t)m * n_leaves,
+    if (r == MR_OK && cudaMemcpyAsync(d_vals, values, sizeof(double) * (size_t)m * n_leaves,
                                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         r = MR_E_CUDA;
     if (r == MR_OK) {
-        h->K.set_leaves(h->d_keys, h->d_T, n_leaves);
+        h->K.set_leaves(d_keys, d_vals, n_leaves);
         for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
         h->t = t;
         h->iters = iters;
@@ -854,6 +1280,8 @@ mr_status mr_create_from_state(const mr_config* cfg, long long n_leaves, const i
         h->pos = 0;
         r = sync_check(h);
     }
+    if (d_keys) cudaFreeAsync(d_keys, h->stream);
+    if (d_vals) cudaFreeAsync(d_vals, h->stream);
     (void)g;
     if (r != MR_OK) {
         mr_destroy(h);
@@ -869,11 +1297,13 @@ mr_status mr_adapt(mr_solver* h)
     if (h->pos != 0) return MR_E_STATE;
     h->wmax_valid = false;
     Grid& g = h->K.g;
+    MR_TRY(set_capacity(h, h->ntot + 1, true)); // room for any tree, compacted at the end
     h->K.leaf_copy(g.lb, g.L, F_QE, F_Q0);
     for (int l = g.L - 1; l >= g.lb; --l) h->K.project(l, PM_Q0);
     MR_TRY(adapt(h, g.lb));
     h->K.leaf_copy(g.lb, g.L, F_Q0, F_QE);
-    return sync_check(h);
+    MR_TRY(sync_check(h));
+    return fit_new_tree(h);
 }
 
 mr_status mr_step(mr_solver* h, double t_target, long long* iters_out)
@@ -883,7 +1313,9 @@ mr_status mr_step(mr_solver* h, double t_target, long long* iters_out)
     const long long it0 = h->iters, nit = 1LL << (h->K.g.L - h->K.g.lb);
     while (h->t < t_target) {
         double dt;
+        MR_TRY(head_enqueue(h)); // read back with the CFL speed
         MR_TRY(cfl_dt(h, &dt));
+        MR_TRY(head_finish(h));
         bool last = false;
         if (h->t + nit * dt >= t_target * (1.0 - 1e-14)) {
             dt = (t_target - h->t) / nit;
@@ -903,6 +1335,7 @@ mr_status mr_iterate(mr_solver* h, double dt, long long n, long long* iters_out)
     const long long it0 = h->iters, nit = 1LL << (h->K.g.L - h->K.g.lb);
     long long i = 0;
     while (i < n) { // whole macro steps at once (a graph), single iterations otherwise
+        if (h->pos == 0) MR_TRY(boundary_check(h)); // capacity rule at the macro-step boundary
         const long long chunk = (h->pos == 0 && n - i >= nit) ? nit : 1;
         MR_TRY(run_iters(h, dt, chunk));
         for (long long k = 0; k < chunk; ++k) h->t += dt;
@@ -940,13 +1373,22 @@ mr_status mr_set_grid_cap(mr_solver* h, int ctas)
     if (h->K.g.gcap == ctas) return MR_OK;
     // a captured macro step holds the old launch shape: drop it once the
     // stream has passed it, and capture again at the next macro step
-    if (h->macro_exec) {
+    if (h->macro_exec || h->head_exec || !h->piece_exec.empty()) {
         MR_CK(cudaStreamSynchronize(h->stream));
-        MR_CK(cudaGraphExecDestroy(h->macro_exec));
-        h->macro_exec = nullptr;
+        drop_graphs(h);
     }
     h->K.g.gcap = ctas;
     return MR_OK;
+}
+
+mr_status mr_reserve_nodes(mr_solver* h, long long nodes)
+{
+    if (!h || nodes < 0) return MR_E_INVALID;
+    if (h->pos != 0) return MR_E_STATE;
+    h->reserved = nodes;
+    if (nodes + 1 <= h->K.g.cap) return MR_OK;
+    MR_TRY(set_capacity(h, nodes + 1, true));
+    return sync_check(h);
 }
 
 mr_status mr_set_launch_mode(mr_solver* h, int mode)
@@ -954,6 +1396,11 @@ mr_status mr_set_launch_mode(mr_solver* h, int mode)
     if (!h || (mode != MR_LAUNCH_PERSISTENT && mode != MR_LAUNCH_GRAPH)) return MR_E_INVALID;
     if (h->pos != 0) return MR_E_STATE;
     h->launch_mode = mode;
+    // the macro-step kernel installs trees without a host check: room for every cell
+    if (mode == MR_LAUNCH_PERSISTENT) {
+        MR_TRY(set_capacity(h, h->ntot + 1, true));
+        MR_TRY(sync_check(h));
+    }
     return MR_OK;
 }
 
@@ -1015,14 +1462,17 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
     if (!buf) return MR_OK;
     if (cap < need) return MR_E_INVALID;
     if (what == MR_READ_LEAF_KEYS || what == MR_READ_LEAF_VALUES) {
+        unsigned char* tmp = nullptr; // transient
+        MR_TRY(scratch(h, &tmp, need));
+        int* keys = what == MR_READ_LEAF_KEYS ? (int*)tmp : nullptr;
+        double* vals = what == MR_READ_LEAF_VALUES ? (double*)tmp : nullptr;
         long long base = 0;
         for (int l = g.lb; l <= g.L; ++l) {
-            if (cnt[l]) h->K.pack(l, base, what == MR_READ_LEAF_KEYS ? h->d_keys : nullptr,
-                                  what == MR_READ_LEAF_VALUES ? h->d_T : nullptr);
+            if (cnt[l]) h->K.pack(l, base, keys, vals);
             base += cnt[l];
         }
-        const void* src = what == MR_READ_LEAF_KEYS ? (const void*)h->d_keys : (const void*)h->d_T;
-        if (need) MR_CK(cudaMemcpyAsync(buf, src, need, cudaMemcpyDeviceToHost, h->stream));
+        if (need) MR_CK(cudaMemcpyAsync(buf, tmp, need, cudaMemcpyDeviceToHost, h->stream));
+        MR_CK(cudaFreeAsync(tmp, h->stream));
     } else if (what == MR_READ_PROFILE) {
         double* P = (double*)buf;
         memset(P, 0, 64 * sizeof(double));
@@ -1039,9 +1489,15 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
             }
         P[5] = (double)(h->K.n + h->stage_launches - h->prof_all0);
         for (int l = 0; l <= LMAX; ++l) P[40 + l] = h->prof_level_ms[l];
-    } else if (what == MR_READ_UNIFORM) {
-        h->K.uniform(h->d_T, h->d_us);
-        MR_CK(cudaMemcpyAsync(buf, h->d_T + g.off[g.L] * m, need, cudaMemcpyDeviceToHost, h->stream));
+    } else if (what == MR_READ_UNIFORM) { // a transient pyramid for the inverse transform
+        double* T = nullptr;
+        uint8_t* us = nullptr;
+        MR_TRY(scratch(h, &T, (size_t)h->ntot * m));
+        MR_TRY(scratch(h, &us, (size_t)h->ntot));
+        h->K.uniform(T, us);
+        MR_CK(cudaMemcpyAsync(buf, T + g.off[g.L] * m, need, cudaMemcpyDeviceToHost, h->stream));
+        MR_CK(cudaFreeAsync(T, h->stream));
+        MR_CK(cudaFreeAsync(us, h->stream));
     } else {
         double* S = (double*)buf;
         memset(S, 0, 64 * sizeof(double));
@@ -1049,6 +1505,8 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
         for (int l = g.lb; l <= g.L; ++l) h->K.mass(l, h->d_part + (size_t)l * MASS_BLOCKS * m);
         MR_CK(cudaMemcpyAsync(part.data(), h->d_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
                               h->stream));
+        int ftop[2] = {0, 0};
+        MR_CK(cudaMemcpyAsync(ftop, g.ftop, sizeof ftop, cudaMemcpyDeviceToHost, h->stream));
         unsigned long long near = 0, upd = 0;
         MR_CK(cudaMemcpyAsync(&near, g.near, sizeof near, cudaMemcpyDeviceToHost, h->stream));
         MR_CK(cudaMemcpyAsync(&upd, g.updates, sizeof upd, cudaMemcpyDeviceToHost, h->stream));
@@ -1061,6 +1519,10 @@ mr_status mr_read(mr_solver* h, int what, void* buf, size_t cap, size_t* used)
         S[5] = (double)nnode;
         S[6] = (double)near;
         S[7] = (double)upd;
+        S[61] = (double)h->halts;     // halted remeshes (node arrays grown mid macro step)
+        S[62] = (double)ftop[0];      // free node slots
+        S[13] = (double)(g.cap - 1);  // node slots
+        S[14] = (double)h->bytes;     // device bytes held
         S[15] = (double)h->pos;
         for (int l = g.lb; l <= g.L; ++l) {
             S[16 + l] = cnt[l];
@@ -1110,7 +1572,12 @@ mr_status mr_profile(mr_solver* h, int enable)
 void mr_destroy(mr_solver* h)
 {
     if (!h) return;
-    if (h->macro_exec) cudaGraphExecDestroy(h->macro_exec);
+    drop_graphs(h);
+    if (h->h_top) {
+        cudaStreamSynchronize(h->stream);
+        cudaFreeHost(h->h_top);
+    }
+    for (void* p : h->node_allocs) cudaFreeAsync(p, h->stream);
     if (h->own_err) {
         cudaStreamSynchronize(h->stream); // the slot may still receive a pending copy
         cudaFreeHost(h->own_err);
@@ -1157,6 +1624,7 @@ struct Progress {
 // queue the CFL reduction of the next macro step
 mr_status progress_start(mr_solver* h, unsigned long long* bits, cudaEvent_t ev, Progress* pg)
 {
+    MR_TRY(head_enqueue(h));
     MR_TRY(cfl_enqueue(h, bits));
     MR_CK(cudaEventRecord(ev, h->stream));
     pg->phase = PG_WAIT;
@@ -1186,6 +1654,8 @@ bool progress_poll(mr_solver* h, double t_target, unsigned long long* bits, cons
         return true;
     }
     const long long nit = 1LL << (h->K.g.L - h->K.g.lb);
+    pg->status = head_finish(h); // the head's count and the free-slot count arrived with the CFL value
+    if (pg->status != MR_OK) return true;
     double dt = cfl_from_bits(h, *bits);
     bool last = false;
     if (h->t + nit * dt >= t_target * (1.0 - 1e-14)) {
@@ -1412,14 +1882,25 @@ mr_request* find_request(mr_server* s, long long id)
     return nullptr;
 }
 
-// projected device bytes of a configuration (the solver's allocations)
+// Projected device bytes of a configuration while it runs: the per-cell
+// arrays, plus node arrays for the projected node count at the capacity rule.
+// Projected nodes: an adapted tree concentrates on fronts of codimension one,
+// about kFrontWidth nodes per finest cell of a (d-1)-dimensional slice, i.e.
+// min(all cells, kFrontWidth 2^{(d-1) L}).  (Creating the solver briefly needs
+// the full tree; mr_create checks that against the free memory.)
+constexpr long long kFrontWidth = 64;
+
 size_t projected_bytes(const mr_config* cfg)
 {
     mr_solver probe;
     probe.dry = true;
     probe.cfg = *cfg;
     layout_alloc(&probe, cfg);
-    return probe.bytes;
+    long long nodes = kFrontWidth << ((cfg->dim - 1) * cfg->max_level);
+    if (nodes > probe.ntot) nodes = probe.ntot;
+    long long slots = nodes + 2 * (nodes / 4 > kMinSlots ? nodes / 4 : kMinSlots) + 1; // the capacity rule
+    if (slots > probe.ntot + 1) slots = probe.ntot + 1;
+    return probe.fixed_bytes + (size_t)slots * per_node_bytes(probe.K.g, probe.reg);
 }
 
 // admit queued requests in arrival order while the budget and the slot
@@ -1455,6 +1936,7 @@ mr_status admit(mr_server* s)
         q->h->async_err = &s->errs[q->slot];
         q->h->launch_mode = MR_LAUNCH_GRAPH; // concurrent requests: as batch instances
         if (s->gcap) mr_set_grid_cap(q->h, s->gcap); // nothing captured yet: cannot fail
+        if (q->h->bytes > q->bytes) q->bytes = q->h->bytes; // the created tree needs more than projected
         s->used += q->bytes;
         q->state = q->h->t < q->t_end ? 1 : 2;
         if (q->state == 1) s->active.push_back(q);
@@ -1557,6 +2039,10 @@ mr_status mr_server_advance(mr_server* s, int* n_active, int* n_queued)
     std::vector<mr_request*> still;
     for (mr_request* q : s->active) {
         progress_poll(q->h, q->t_end, &s->bits[q->slot], &s->errs[q->slot], q->ev, &q->pg);
+        if (q->h->bytes > q->bytes) { // its node arrays grew: charged from now on
+            s->used += q->h->bytes - q->bytes;
+            q->bytes = q->h->bytes;
+        }
         if (q->pg.phase == PG_DONE) {
             q->status = q->pg.status;
             cudaEventRecord(q->fin, q->st);

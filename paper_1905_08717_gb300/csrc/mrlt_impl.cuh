@@ -2,22 +2,33 @@
 // MRLT/NERK library (private to the library; the public C-ABI is mrlt.h).
 //
 // Data layout in HBM (one solver instance):
-//   every level l in [min_level, L] is a dense grid of N_l = 2^{d l} cells,
-//   cell id = i + n_l (j + n_l k), n_l = 2^l.  All levels of one quantity
-//   live in one "pyramid" allocation at offset off[l] (cells).
-//   - status pyramid (uint8): 0 absent, 1 leaf, 2 internal node
-//   - field pyramids (SoA per level: [off_l * m + v * N_l + id]), float64, or
-//     float32 in the mixed-precision mode (the state is stored, and the stage
-//     arithmetic done, in FP32; registers and the detail test stay FP64):
+//   every level l in [min_level, L] indexes its N_l = 2^{d l} cells as
+//   id = i + n_l (j + n_l k), n_l = 2^l; the per-cell maps of all levels live
+//   in one "pyramid" allocation at offset off[l] (cells):
+//   - status (uint8): 0 absent, 1 leaf, 2 internal node; refinement flags (uint8)
+//   - slot (int32): the node's slot in the node arrays, -1 when absent
+//   The values live only where nodes exist: node arrays of `cap` slots, each
+//   node's m variables contiguous ([slot][v]); slot 0 is a sink that never
+//   belongs to a node (see the capacity rule in mrlt_api.cu):
+//   - fields, float64, or float32 in the mixed-precision mode (the state is
+//     stored, and the stage arithmetic done, in FP32; registers and the detail
+//     test stay FP64):
 //       Q0 q^n, Q1 q*, Q2 q**, QE q^{n+1} (leaves: compact RK stages of Sec. 3;
 //       internal nodes: the projections / refreshed values of Algs. 3-9),
 //       XH half-step value (Eq. 17), NH, N1, N3 the NERK theta = 1/2, 1/4, 3/4
 //       values of internal nodes.  Leaves never store NERK values: they are
 //       recomputed from Q0, Q1, Q2, QE where needed (same polynomial).
-//   - register pyramids (float64, [off_l * nf * m + (face * m + v) * N_l + id]):
-//       coarse-side (RC) and fine-side (RF) time-integrated face fluxes.
+//   - registers (float64, [slot][face][v]): the time-integrated flux through
+//       each face of a leaf whose neighbour across it is on another level (a
+//       coarse leaf at a face to finer nodes, or a fine leaf at a face to a
+//       coarser leaf).  One array serves both roles: the kind of a face cannot
+//       change while its register holds a value (the restricted remesh keeps
+//       both sides until the coarse step ends, when the reflux clears them).
 //   - per-level compact lists (int32) of leaves and internal nodes, ascending
 //     cell id, rebuilt after every remesh by warp-ballot stream compaction.
+//   Free slots form a stack (fstack, ftop[0] entries); a remesh releases the
+//   slots of removed nodes, then pops slots for new nodes (ftop[1] counts the
+//   pops until the next compaction commits them).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -38,14 +49,17 @@ constexpr int kTileThreads1 = 128, kTileThreads2 = 256, kTileThreads3 = 256;
 enum Field { F_Q0 = 0, F_Q1, F_Q2, F_QE, F_XH, F_NH, F_N1, F_N3, NFIELD };
 enum Kind { K_WALL = 0, K_LEAF = 1, K_FINER = 2, K_COARSER = 3 };
 enum FlagBits { FL_SIG = 1, FL_BIG = 2, FL_DES = 4, FL_ALLOW = 8, FL_REF = 16 };
-enum ErrBits { ERR_INDEX = 1, ERR_SOURCE = 2, ERR_NONFINITE = 4, ERR_REFLUX = 8, ERR_TIMEOUT = 16 };
+enum ErrBits { ERR_INDEX = 1, ERR_SOURCE = 2, ERR_NONFINITE = 4, ERR_REFLUX = 8, ERR_TIMEOUT = 16, ERR_CAPACITY = 32 };
 
 struct Grid {
     uint8_t* st;
     uint8_t* flag;
-    void* f[NFIELD];                // field pyramids: double, or float when prec = 1
-    double* rc;
-    double* rf;
+    int* slot;                      // per cell: node slot, -1 when absent
+    int* fstack;                    // free slots
+    int* ftop;                      // [0] free slots on the stack, [1] pops not yet committed
+    long long cap;                  // node slots (slot 0 is the sink)
+    void* f[NFIELD];                // node fields: double, or float when prec = 1
+    double* rg;                     // flux registers of the nodes, [slot][face][v]
     int* leaves;
     int* inner;
     int* counts;                    // [0..LMAX] leaves, [LMAX+1..] internal nodes, [2(LMAX+1)..] active tiles
@@ -59,6 +73,7 @@ struct Grid {
     unsigned long long* updates;
     unsigned long long* work;       // [(LMAX+1) * 4]: leaf-stages per level and stage
     double* dtp;                    // fine step dt of the current macro step (device scalar)
+    int* room;                      // [0] refinement flags being counted, [1] halt: iteration + 1, [2] nodes needed
     long long off[LMAX + 1];
     long long N[LMAX + 1];
     int n[LMAX + 1];
@@ -88,6 +103,19 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+
+// A remesh inside a macro step whose new tree would need more node slots than
+// the arrays hold halts the solver's device work (room[1] != 0): every later
+// kernel of the fine iterations returns at its start, until the host has
+// grown the arrays, cleared the halt and resumed at the halted iteration.
+// Read after pdl_enter, so that a halt set by an earlier kernel is visible.
+__device__ __forceinline__ bool halted(const Grid& g) { return g.room[1] != 0; }
+
+#define MRLT_ENTER(g)         \
+    do {                      \
+        pdl_enter();          \
+        if (halted(g)) return; \
+    } while (0)
 
 // Launch with programmatic stream serialisation: the kernel may be launched
 // before its predecessor in the stream has finished; it waits in pdl_enter().
@@ -158,11 +186,23 @@ __device__ __forceinline__ void cell_xyz(const Grid& g, int l, long long id, int
     c[2] = g.d > 2 ? (int)(id >> (2 * l)) : 0;
 }
 
-// level l of field f, stored as T (double, or float in the mixed mode)
+// the m values of field f of the node in slot sl, stored as T (double, or
+// float in the mixed mode); a negative slot (an absent cell) reads the sink
 template <class T>
-__device__ __forceinline__ T* fld(const Grid& g, int f, int l)
+__device__ __forceinline__ T* nd(const Grid& g, int f, int sl)
 {
-    return static_cast<T*>(g.f[f]) + g.off[l] * g.m;
+    return static_cast<T*>(g.f[f]) + (long long)(sl < 0 ? 0 : sl) * g.m;
+}
+
+__device__ __forceinline__ int slot_of(const Grid& g, int l, long long id)
+{
+    return g.slot[g.off[l] + id];
+}
+
+// registers of the node in slot sl: [face][v]
+__device__ __forceinline__ double* regs(double* r, const Grid& g, int sl)
+{
+    return r + (long long)(sl < 0 ? 0 : sl) * g.nf * g.m;
 }
 
 __device__ __forceinline__ uint8_t status(const Grid& g, int l, long long id)
@@ -170,7 +210,7 @@ __device__ __forceinline__ uint8_t status(const Grid& g, int l, long long id)
     return g.st[g.off[l] + id];
 }
 
-// Value of stored node (l, id) (status st) as seen by the stencil of a
+// Value of the stored node of level l in slot sl (status st) as seen by the stencil of a
 // level-u leaf at stage x.s of the current iteration: the exposure table of
 // Secs. 4.1-4.3 / Algs. 3-9.  Leaves recompute their NERK values from the
 // stage values: with k1 = q* - q^n and k2 the second stage increment
@@ -178,80 +218,79 @@ __device__ __forceinline__ uint8_t status(const Grid& g, int l, long long id)
 // q(theta) = q^n + (theta - theta^2/2) k1 + theta^2/2 k2 (Sec. 3 NERK2).
 // T is the storage type of the fields, O the arithmetic type of the result.
 template <int M, class T, class O>
-__device__ __forceinline__ void expose(const Grid& g, const Ctx& x, int l, long long id, int st, O* out)
+__device__ __forceinline__ void expose(const Grid& g, const Ctx& x, int l, int sl, int st, O* out)
 {
-    const long long N = g.N[l];
-    const T* q0 = fld<T>(g, F_Q0, l) + id;
-    const T* q1 = fld<T>(g, F_Q1, l) + id;
-    const T* q2 = fld<T>(g, F_Q2, l) + id;
-    const T* qe = fld<T>(g, F_QE, l) + id;
+    const T* q0 = nd<T>(g, F_Q0, sl);
+    const T* q1 = nd<T>(g, F_Q1, sl);
+    const T* q2 = nd<T>(g, F_Q2, sl);
+    const T* qe = nd<T>(g, F_QE, sl);
     const int s = x.s;
     const int rel = l - x.u;
     if (s == 0 || (s == 1 && g.gts) || (s == 1 && (rel >= 0 || l >= x.lmin))) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = O(q0[v * N]);
+        for (int v = 0; v < M; ++v) out[v] = O(q0[v]);
         return;
     }
     if (g.gts) {
         const T* a = s == 2 ? q1 : q2;
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = O(a[v * N]);
+        for (int v = 0; v < M; ++v) out[v] = O(a[v]);
         return;
     }
     if (s == 1) { // coarser level lmin-1, mid-step: theta = 1/2 value
         if (g.rk == 3) {
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = O(q2[v * N]);
+            for (int v = 0; v < M; ++v) out[v] = O(q2[v]);
         } else if (st == 1) {
 #pragma unroll
             for (int v = 0; v < M; ++v)
-                out[v] = O(0.5) * O(q0[v * N]) + O(0.25) * O(q1[v * N]) + O(0.25) * O(qe[v * N]);
+                out[v] = O(0.5) * O(q0[v]) + O(0.25) * O(q1[v]) + O(0.25) * O(qe[v]);
         } else {
-            const T* nh = fld<T>(g, F_NH, l) + id;
+            const T* nh = nd<T>(g, F_NH, sl);
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = O(nh[v * N]);
+            for (int v = 0; v < M; ++v) out[v] = O(nh[v]);
         }
         return;
     }
     if (s == 2) {
         if (rel == 0) {
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = O(q1[v * N]);
+            for (int v = 0; v < M; ++v) out[v] = O(q1[v]);
         } else if (rel == 1) {
             if (st == 1) { // Eq. 14: q* + k2
                 if (g.rk == 2) {
 #pragma unroll
-                    for (int v = 0; v < M; ++v) out[v] = O(2) * O(qe[v * N]) - O(q0[v * N]);
+                    for (int v = 0; v < M; ++v) out[v] = O(2) * O(qe[v]) - O(q0[v]);
                 } else {
 #pragma unroll
-                    for (int v = 0; v < M; ++v) out[v] = O(4) * O(q2[v * N]) - O(3) * O(q0[v * N]);
+                    for (int v = 0; v < M; ++v) out[v] = O(4) * O(q2[v]) - O(3) * O(q0[v]);
                 }
             } else { // Eq. 15
 #pragma unroll
-                for (int v = 0; v < M; ++v) out[v] = O(2) * O(q1[v * N]) - O(q0[v * N]);
+                for (int v = 0; v < M; ++v) out[v] = O(2) * O(q1[v]) - O(q0[v]);
             }
         } else if (l >= x.lmin) { // half step of the coarser level
             if (st == 1) {
 #pragma unroll
-                for (int v = 0; v < M; ++v) out[v] = O(q0[v * N]) + O(0.5) * (O(q1[v * N]) - O(q0[v * N]));
+                for (int v = 0; v < M; ++v) out[v] = O(q0[v]) + O(0.5) * (O(q1[v]) - O(q0[v]));
             } else {
-                const T* xh = fld<T>(g, F_XH, l) + id;
+                const T* xh = nd<T>(g, F_XH, sl);
 #pragma unroll
-                for (int v = 0; v < M; ++v) out[v] = O(xh[v * N]);
+                for (int v = 0; v < M; ++v) out[v] = O(xh[v]);
             }
         } else { // end of the mid-step coarser level
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = O(qe[v * N]);
+            for (int v = 0; v < M; ++v) out[v] = O(qe[v]);
         }
         return;
     }
     // stage 3
     if (rel == 0) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = O(q2[v * N]);
+        for (int v = 0; v < M; ++v) out[v] = O(q2[v]);
     } else if (rel == 1) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) out[v] = O(qe[v * N]);
+        for (int v = 0; v < M; ++v) out[v] = O(qe[v]);
     } else {
         const bool act = l >= x.lmin;
         if (st == 1) {
@@ -259,15 +298,15 @@ __device__ __forceinline__ void expose(const Grid& g, const Ctx& x, int l, long 
             const O b2 = act ? O(1.0 / 32.0) : O(9.0 / 32.0);
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                const O a0 = O(q0[v * N]), a1 = O(q1[v * N]);
+                const O a0 = O(q0[v]), a1 = O(q1[v]);
                 const O k1 = a1 - a0;
-                const O k2 = O(4) * O(q2[v * N]) - O(3) * a0 - a1;
+                const O k2 = O(4) * O(q2[v]) - O(3) * a0 - a1;
                 out[v] = a0 + b1 * k1 + b2 * k2;
             }
         } else {
-            const T* nn = fld<T>(g, act ? F_N1 : F_N3, l) + id;
+            const T* nn = nd<T>(g, act ? F_N1 : F_N3, sl);
 #pragma unroll
-            for (int v = 0; v < M; ++v) out[v] = O(nn[v * N]);
+            for (int v = 0; v < M; ++v) out[v] = O(nn[v]);
         }
     }
 }
@@ -314,12 +353,13 @@ __device__ __forceinline__ void predict(const Grid& g, const Ctx& x, int l, cons
                 const int xx = wrap_or_mirror(g, pl, 0, P0 + dxx, neg);
                 const long long id = cell_id(g, pl, xx, y, z);
                 const int st = status(g, pl, id);
+                const int sl = slot_of(g, pl, id);
                 if (st == 0) {
                     atomicOr(g.err, ERR_SOURCE);
                     continue;
                 }
                 O val[M];
-                expose<M, T, O>(g, x, pl, id, st, val);
+                expose<M, T, O>(g, x, pl, sl, st, val);
                 const O w0 = wyz * O(pw(a0, dxx));
                 const O w = neg ? -w0 : w0; // an odd-mirror ghost enters negated
 #pragma unroll
@@ -357,12 +397,13 @@ __device__ __forceinline__ void predict_children(const Grid& g, const Ctx& x, in
                 const int xx = wrap_or_mirror(g, l, 0, c[0] + dxx, neg);
                 const long long id = cell_id(g, l, xx, y, z);
                 const int st = status(g, l, id);
+                const int sl = slot_of(g, l, id);
                 if (st == 0) {
                     atomicOr(g.err, ERR_SOURCE);
                     continue;
                 }
                 double val[M];
-                expose<M, T, double>(g, x, l, id, st, val);
+                expose<M, T, double>(g, x, l, sl, st, val);
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {
                     const double wz = D > 2 ? pw((k >> 2) & 1, dz) : 1.0;
@@ -387,7 +428,7 @@ __device__ __forceinline__ void value_at(const Grid& g, const Ctx& x, int l, con
     for (int k = 0; k < D; ++k) q[k] = wrap_or_mirror(g, l, k, p[k], neg);
     const long long id = cell_id(g, l, q[0], q[1], q[2]);
     const int st = status(g, l, id);
-    if (st) expose<M, T, O>(g, x, l, id, st, out);
+    if (st) expose<M, T, O>(g, x, l, slot_of(g, l, id), st, out);
     else predict<D, M, T, O>(g, x, l, q, out);
     if (neg) {
 #pragma unroll

@@ -223,6 +223,9 @@ k_macro(const __grid_constant__ Grid g, MacroArgs a)
                 mph_close<D>(g, l);
                 MRLT_SYNC();
             }
+            phase(PH_ADAPT, 5);
+            dev_release(g, la); // slots of removed nodes back on the free stack
+            MRLT_SYNC();
             for (int l = la; l <= L; ++l) {
                 phase(PH_ADAPT, 5);
                 mph_apply<D, M, R>(g, l, la);

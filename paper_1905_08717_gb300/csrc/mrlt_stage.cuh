@@ -19,37 +19,33 @@ namespace mrlt {
 // qs is the leaf's own value at stage s (q^n, q*, q** for s = 1, 2, 3: its
 // exposure, already staged in shared memory) and q0 its q^n (s >= 2).
 template <int M, class R>
-__device__ __forceinline__ void rk_update(const Grid& g, int u, long long id, int s, R dtl, const R* f, const R* q0,
-                                          const R* qs)
+__device__ __forceinline__ void rk_update(const Grid& g, int sl, int s, R dtl, const R* f, const R* q0, const R* qs)
 {
-    const long long N = g.N[u];
-    R* q1 = fld<R>(g, F_Q1, u) + id;
-    R* q2 = fld<R>(g, F_Q2, u) + id;
-    R* qe = fld<R>(g, F_QE, u) + id;
+    R* q1 = nd<R>(g, F_Q1, sl);
+    R* q2 = nd<R>(g, F_Q2, sl);
+    R* qe = nd<R>(g, F_QE, sl);
 #pragma unroll
     for (int v = 0; v < M; ++v) {
         const R kk = dtl * f[v];
         if (s == 1) {
-            q1[v * N] = qs[v] + kk;
+            q1[v] = qs[v] + kk;
         } else if (s == 2) {
-            if (g.rk == 2) qe[v * N] = R(0.5) * q0[v] + R(0.5) * qs[v] + R(0.5) * kk;
-            else q2[v * N] = R(0.75) * q0[v] + R(0.25) * qs[v] + R(0.25) * kk;
+            if (g.rk == 2) qe[v] = R(0.5) * q0[v] + R(0.5) * qs[v] + R(0.5) * kk;
+            else q2[v] = R(0.75) * q0[v] + R(0.25) * qs[v] + R(0.25) * kk;
         } else {
-            qe[v * N] = R(1.0 / 3.0) * q0[v] + R(2.0 / 3.0) * qs[v] + R(2.0 / 3.0) * kk;
+            qe[v] = R(1.0 / 3.0) * q0[v] + R(2.0 / 3.0) * qs[v] + R(2.0 / 3.0) * kk;
         }
     }
 }
 
 // flux registers (conservation across levels): dt_l b_s F at coarse-fine faces
 template <int M>
-__device__ __forceinline__ void reg_add(const Grid& g, int u, long long id, int fi, int kind, double bw,
-                                        const double* F)
+__device__ __forceinline__ void reg_add(const Grid& g, int sl, int fi, int kind, double bw, const double* F)
 {
     if (kind != K_FINER && kind != K_COARSER) return;
-    const long long N = g.N[u];
-    double* R = (kind == K_FINER ? g.rc : g.rf) + g.off[u] * g.nf * g.m + id;
+    double* R = regs(g.rg, g, sl); // coarse side (K_FINER) or fine side (K_COARSER) of the face
 #pragma unroll
-    for (int v = 0; v < M; ++v) R[(fi * M + v) * N] += bw * F[v];
+    for (int v = 0; v < M; ++v) R[fi * M + v] += bw * F[v];
 }
 
 // Tile shapes of the tiled stage kernel: a CTA of THREADS threads owns
@@ -127,44 +123,43 @@ __device__ __forceinline__ void block_append2(bool ta, bool tb, int item, short*
 
 // Value of the stored finer-level node at in-box coordinates q of level l =
 // u + 1 as the level-u stencil sees it at stage x.s (the rel = +1 rows of
-// expose()), with its status and every field the choice may need loaded at
-// once: one memory round trip instead of status, then fields.  Returns false
-// (out untouched) when the cell is absent.
+// expose()): its status and slot, then every field the choice may need,
+// loaded at once.  Returns false (out untouched) when the cell is absent.
 template <int M, class T>
 __device__ __forceinline__ bool finer_exposure(const Grid& g, const Ctx& x, int l, const int q[3], T* out)
 {
     const long long id = cell_id(g, l, q[0], q[1], q[2]);
-    const long long N = g.N[l];
-    const T* q0 = fld<T>(g, F_Q0, l) + id;
     const int st = status(g, l, id);
+    const int sl = slot_of(g, l, id);
+    const T* q0 = nd<T>(g, F_Q0, sl);
     if (x.s <= 1) {
         T a[M];
 #pragma unroll
-        for (int v = 0; v < M; ++v) a[v] = q0[v * N];
+        for (int v = 0; v < M; ++v) a[v] = q0[v];
         if (st == 0) return false;
 #pragma unroll
         for (int v = 0; v < M; ++v) out[v] = a[v];
         return true;
     }
     if (g.gts || x.s == 3) { // global step: q* / q**; LT stage 3: q^{n+1} of the first sub-step
-        const T* a = fld<T>(g, g.gts ? (x.s == 2 ? F_Q1 : F_Q2) : F_QE, l) + id;
+        const T* a = nd<T>(g, g.gts ? (x.s == 2 ? F_Q1 : F_Q2) : F_QE, sl);
         T b[M];
 #pragma unroll
-        for (int v = 0; v < M; ++v) b[v] = a[v * N];
+        for (int v = 0; v < M; ++v) b[v] = a[v];
         if (st == 0) return false;
 #pragma unroll
         for (int v = 0; v < M; ++v) out[v] = b[v];
         return true;
     }
     // LT stage 2: leaf Eq. 14 (q* + k2), internal node Eq. 15 (2 q* - q^n)
-    const T* q1 = fld<T>(g, F_Q1, l) + id;
-    const T* qx = fld<T>(g, g.rk == 2 ? F_QE : F_Q2, l) + id;
+    const T* q1 = nd<T>(g, F_Q1, sl);
+    const T* qx = nd<T>(g, g.rk == 2 ? F_QE : F_Q2, sl);
     T a0[M], a1[M], ax[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) {
-        a0[v] = q0[v * N];
-        a1[v] = q1[v * N];
-        ax[v] = qx[v * N];
+        a0[v] = q0[v];
+        a1[v] = q1[v];
+        ax[v] = qx[v];
     }
     if (st == 0) return false;
     if (st == 1) {
@@ -233,7 +228,9 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
     R (*sF)[NF] = reinterpret_cast<R (*)[NF]>(rbase + sizeof(R) * M * NB);
     R (*sFine)[M][NPF] = reinterpret_cast<R (*)[M][NPF]>(rbase + sizeof(R) * M * (NB + NF));
     __shared__ uint8_t sSt[NB], sNeed[NB];  // status; needed | stored << 1
+    __shared__ int sSlot[NB];               // node slots of the block cells
     __shared__ uint8_t sPSt[PB], sPNeg[PB], sPNeed[PB];
+    __shared__ int sPSlot[PB];
     __shared__ short sList[NB], sList2[NB]; // stored, virtual cells
     __shared__ short sFace1[NF], sFace2[NF]; // faces against an internal node, plain faces
     __shared__ short sPList[PB];
@@ -371,7 +368,9 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
         int qx, qy = 0, qz = 0;
         const bool inb = in_box(g, u, 0, ox + bx - H, &qx) && (D < 2 || in_box(g, u, 1, oy + by - H, &qy)) &&
                          (D < 3 || in_box(g, u, 2, oz + bz - H, &qz));
-        sSt[b] = inb ? status(g, u, cell_id(g, u, qx, qy, qz)) : OUT;
+        const long long id = cell_id(g, u, qx, qy, qz);
+        sSt[b] = inb ? status(g, u, id) : OUT;
+        sSlot[b] = inb ? slot_of(g, u, id) : -1;
     }
     if (pstage)
         for (int pb = tid; pb < PB; pb += NT) {
@@ -380,7 +379,9 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
             const int px = wrap_or_mirror(g, u - 1, 0, pox + i, neg);
             const int py = D > 1 ? wrap_or_mirror(g, u - 1, 1, poy + j, neg) : 0;
             const int pz = D > 2 ? wrap_or_mirror(g, u - 1, 2, poz + kk, neg) : 0;
-            sPSt[pb] = status(g, u - 1, cell_id(g, u - 1, px, py, pz));
+            const long long pid = cell_id(g, u - 1, px, py, pz);
+            sPSt[pb] = status(g, u - 1, pid);
+            sPSlot[pb] = slot_of(g, u - 1, pid);
             sPNeg[pb] = (uint8_t)neg;
             sPNeed[pb] = 0;
         }
@@ -444,22 +445,16 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
     const bool own_leaf = s >= 2 && tid < NC &&
                           tile_leaf(H + tid % TX, D > 1 ? H + (tid / TX) % TY : 0, D > 2 ? H + tid / (TX * TY) : 0);
     if (own_leaf) {
-        const long long N = g.N[u];
-        const R* q0 = fld<R>(g, F_Q0, u) + cell_id(g, u, ox + tid % TX, D > 1 ? oy + (tid / TX) % TY : 0,
-                                                   D > 2 ? oz + tid / (TX * TY) : 0);
+        const int b = (D > 2 ? H + tid / (TX * TY) : 0) * SZ + (D > 1 ? H + (tid / TX) % TY : 0) * SY + H + tid % TX;
+        const R* q0 = nd<R>(g, F_Q0, sSlot[b]);
 #pragma unroll
-        for (int v = 0; v < M; ++v) q0r[v] = q0[v * N];
+        for (int v = 0; v < M; ++v) q0r[v] = q0[v];
     }
     for (int t = tid; t < nst + npl; t += NT) {
         R W[M];
         if (t < nst) {
             const int b = sList[t];
-            const int bx = b % BX, by = (b / BX) % BY, bz = b / SZ;
-            int qx, qy = 0, qz = 0;
-            in_box(g, u, 0, ox + bx - H, &qx);
-            if (D > 1) in_box(g, u, 1, oy + by - H, &qy);
-            if (D > 2) in_box(g, u, 2, oz + bz - H, &qz);
-            expose<M, R, R>(g, x, u, cell_id(g, u, qx, qy, qz), sSt[b], W);
+            expose<M, R, R>(g, x, u, sSlot[b], sSt[b], W);
             R P[M];
             recon_vars<EQ, D, M, R>(g, W, P);
 #pragma unroll
@@ -471,13 +466,9 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
             const int pb = sPList[t - nst];
             const int st = sPSt[pb];
             if (st == 0) continue; // predict() flags the absent source when it reads it
-            const int i = pb % PBX, j = (pb / PBX) % PBY, kk = pb / PSZ;
-            int neg = 0;
-            const int px = wrap_or_mirror(g, u - 1, 0, pox + i, neg);
-            const int py = D > 1 ? wrap_or_mirror(g, u - 1, 1, poy + j, neg) : 0;
-            const int pz = D > 2 ? wrap_or_mirror(g, u - 1, 2, poz + kk, neg) : 0;
-            expose<M, R, R>(g, x, u - 1, cell_id(g, u - 1, px, py, pz), st, W);
+            expose<M, R, R>(g, x, u - 1, sPSlot[pb], st, W);
             // an odd-mirror ghost enters negated: (-w) v = w (-v) exactly
+            const bool neg = sPNeg[pb] != 0;
 #pragma unroll
             for (int v = 0; v < M; ++v) sPW[v][pb] = neg ? -W[v] : W[v];
         }
@@ -668,7 +659,7 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
         const int bx = H + i, by = D > 1 ? H + j : 0, bz = D > 2 ? H + kz : 0;
         const int b = bz * SZ + by * SY + bx;
         if (tile_leaf(bx, by, bz)) {
-        const long long id = cell_id(g, u, ox + i, oy + j, oz + kz);
+        const int sl = sSlot[b];
         R self[M], f[M], q0p[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) self[v] = sW[v][b];
@@ -703,11 +694,11 @@ __device__ __forceinline__ void stage_tiles(const Grid& g, int lo, int hi, int s
 #pragma unroll
             for (int v = 0; v < M; ++v) f[v] += (R(Fm[v]) - R(Fp[v])) * idx;
             if (reg) {
-                reg_add<M>(g, u, id, 2 * k, km, bw, Fm);
-                reg_add<M>(g, u, id, 2 * k + 1, kp, bw, Fp);
+                reg_add<M>(g, sl, 2 * k, km, bw, Fm);
+                reg_add<M>(g, sl, 2 * k + 1, kp, bw, Fp);
             }
         }
-        rk_update<M, R>(g, u, id, s, R(dtl), f, q0p, self);
+        rk_update<M, R>(g, sl, s, R(dtl), f, q0p, self);
         }
     }
     __syncthreads(); // shared arrays are reused by the next tile
@@ -718,7 +709,7 @@ template <int EQ, int D, class R>
 __global__ void __launch_bounds__(Tile<D>::THREADS)
 k_stage_tile(const __grid_constant__ Grid g, int lo, int hi, int s, int lmin, double bstage, int reg)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     extern __shared__ __align__(16) unsigned char smem[];
     stage_tiles<EQ, D, R>(g, lo, hi, s, lmin, bstage, reg, smem);
 }

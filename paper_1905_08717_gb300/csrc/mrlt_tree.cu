@@ -27,83 +27,83 @@ static inline int blocks_list(const Grid& g, int l)
 template <class T>
 __global__ void k_leaf_copy(const __grid_constant__ Grid g, int lo, int hi, int from, int to)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_leaf_copy<T>(g, lo, hi, from, to);
 }
 
 template <int D, class T>
 __global__ void k_project(const __grid_constant__ Grid g, int l, int mode)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_project<D, T>(g, l, mode);
 }
 
 template <int D, int M, class T>
 __global__ void k_detail(const __grid_constant__ Grid g, int lo, int hi)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_detail<D, M, T>(g, lo, hi);
 }
 
 template <int D>
 __global__ void k_desire(const __grid_constant__ Grid g, int lo, int hi, int la)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_desire<D>(g, lo, hi, la);
 }
 
 template <int D>
 __global__ void k_allow(const __grid_constant__ Grid g, int lo, int hi, int la)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_allow<D>(g, lo, hi, la);
 }
 
 template <int D>
 __global__ void k_close(const __grid_constant__ Grid g, int l)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_close<D>(g, l);
 }
 
 template <int D, int M, class T>
 __global__ void k_apply(const __grid_constant__ Grid g, int l, int la)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_apply<D, M, T>(g, l, la);
 }
 
 // compaction of levels lo..hi: chunks of NTHREADS cells, one block each
 __global__ void k_cmp_count(const __grid_constant__ Grid g, LevelChunks lc, int* bc)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     chunk_count<NTHREADS>(g, lc, blockIdx.x, bc);
 }
 
 // exclusive scan of the per-chunk counts, one block per level
 __global__ void k_cmp_scan(const __grid_constant__ Grid g, LevelChunks lc, int* bc)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     level_scan<1024>(g, lc, lc.lo + blockIdx.x, bc);
 }
 
 __global__ void k_cmp_scatter(const __grid_constant__ Grid g, LevelChunks lc, const int* bc)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     chunk_scatter<NTHREADS>(g, lc, blockIdx.x, bc);
 }
 
 // ordered list of the active tiles of level lo + blockIdx.x (one block per level)
 __global__ void k_tile_list(const __grid_constant__ Grid g, int lo)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     level_tile_list<1024>(g, lo + blockIdx.x);
 }
 
 template <int D, class T>
 __global__ void k_reflux(const __grid_constant__ Grid g, int lo, int hi)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_reflux<D, T>(g, lo, hi);
 }
 
@@ -111,14 +111,14 @@ __global__ void k_reflux(const __grid_constant__ Grid g, int lo, int hi)
 template <class T>
 __global__ void k_scale(const __grid_constant__ Grid g, int l)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_scale<T>(g, l, l);
 }
 
 template <class T>
 __global__ void k_finite(const __grid_constant__ Grid g, int l)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     dev_finite<T>(g, l, l);
 }
 
@@ -136,7 +136,7 @@ __global__ void k_mass(Grid g, int l, double* part)
         for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
              t += (long long)gridDim.x * blockDim.x) {
             const long long id = list[t];
-            if (id >= 0 && id < N) acc += double(fld<T>(g, F_QE, l)[v * N + id]);
+            if (id >= 0 && id < N) acc += double(nd<T>(g, F_QE, slot_of(g, l, id))[v]);
         }
         sh[threadIdx.x] = acc;
         __syncthreads();
@@ -170,7 +170,7 @@ __global__ void k_pack(Grid g, int l, long long base, int* keys, double* vals)
             K[3] = c[2];
         }
         if (vals)
-            for (int v = 0; v < g.m; ++v) vals[(base + t) * g.m + v] = double(fld<T>(g, F_QE, l)[v * N + id]);
+            for (int v = 0; v < g.m; ++v) vals[(base + t) * g.m + v] = double(nd<T>(g, F_QE, slot_of(g, l, id))[v]);
     }
 }
 
@@ -190,7 +190,7 @@ __global__ void k_uni_up(Grid g, int l, double* T, uint8_t* us)
         const int s = status(g, l, id);
         us[g.off[l] + id] = s != 0;
         if (s == 1) {
-            for (int v = 0; v < g.m; ++v) Tl[v * N + id] = double(fld<F>(g, F_QE, l)[v * N + id]);
+            for (int v = 0; v < g.m; ++v) Tl[v * N + id] = double(nd<F>(g, F_QE, slot_of(g, l, id))[v]);
         } else if (s == 2) {
             int c[3];
             cell_xyz(g, l, id, c);
@@ -283,10 +283,18 @@ static void adapt_dm(Launcher& L, int la)
     for (int l = g.L - 1; l > la; --l, ++L.n) pdl_launch(k_close<D>, blocks_dense(g.N[l - 1]), NTHREADS, 0, L.st, g, l);
 }
 
+__global__ void k_release(const __grid_constant__ Grid g, int la)
+{
+    MRLT_ENTER(g);
+    dev_release(g, la);
+}
+
 template <int D, int M>
 static void apply_dm(Launcher& L, int la)
 {
     const Grid& g = L.g;
+    pdl_launch(k_release, blocks_list(g, g.L), NTHREADS, 0, L.st, g, la);
+    ++L.n;
     for (int l = la; l <= g.L; ++l, ++L.n) {
         if (g.prec) pdl_launch(k_apply<D, M, float>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
         else pdl_launch(k_apply<D, M, double>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
@@ -343,7 +351,7 @@ void Launcher::reflux(int lo, int hi)
 
 __global__ void k_scale_init(Grid g)
 {
-    pdl_enter();
+    MRLT_ENTER(g);
     if (threadIdx.x < MMAX) g.scale_bits[threadIdx.x] = (unsigned long long)__double_as_longlong(1e-14);
 }
 
@@ -374,10 +382,10 @@ __global__ void k_set_leaves(Grid g, const int* keys, const double* vals, long l
             atomicOr(g.err, ERR_INDEX);
             continue;
         }
-        const long long N = g.N[l];
-        T* q0 = fld<T>(g, F_Q0, l) + id;
-        T* qe = fld<T>(g, F_QE, l) + id;
-        for (int v = 0; v < g.m; ++v) q0[v * N] = qe[v * N] = T(vals[t * g.m + v]);
+        const int sl = slot_of(g, l, id);
+        T* q0 = nd<T>(g, F_Q0, sl);
+        T* qe = nd<T>(g, F_QE, sl);
+        for (int v = 0; v < g.m; ++v) q0[v] = qe[v] = T(vals[t * g.m + v]);
     }
 }
 
@@ -388,18 +396,179 @@ void Launcher::set_leaves(const int* keys, const double* vals, long long count)
     ++n;
 }
 
-// finest-level data uploaded as double, stored in the field's type
+// finest-level data (host layout [v][cell], uploaded as double) stored in
+// q^n of the finest nodes, in the fields' type
+template <class T>
 __global__ void k_store_finest(Grid g, const double* src)
 {
     pdl_enter();
-    const long long n = g.N[g.L] * g.m;
-    float* dst = static_cast<float*>(g.f[F_Q0]) + g.off[g.L] * g.m;
-    GRID_STRIDE(i, n) dst[i] = float(src[i]);
+    const long long N = g.N[g.L];
+    GRID_STRIDE(id, N)
+    {
+        T* q0 = nd<T>(g, F_Q0, slot_of(g, g.L, id));
+        for (int v = 0; v < g.m; ++v) q0[v] = T(src[v * N + id]);
+    }
 }
 
 void Launcher::store_finest(const double* src)
 {
-    pdl_launch(k_store_finest, blocks_dense(g.N[g.L] * g.m), NTHREADS, 0, st, g, src);
+    if (g.prec) pdl_launch(k_store_finest<float>, blocks_dense(g.N[g.L]), NTHREADS, 0, st, g, src);
+    else pdl_launch(k_store_finest<double>, blocks_dense(g.N[g.L]), NTHREADS, 0, st, g, src);
+    ++n;
+}
+
+// every cell of levels lb..L a node in slot 1 + (its offset in the
+// pyramid): the full tree of a new solver; the free stack holds the rest
+__global__ void k_slots_full(Grid g, long long ntot)
+{
+    pdl_enter();
+    GRID_STRIDE(i, ntot) g.slot[g.off[g.lb] + i] = (int)(1 + i);
+    const long long nfree = g.cap - 1 - ntot;
+    GRID_STRIDE(k, nfree) g.fstack[k] = (int)(g.cap - 1 - k);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g.ftop[0] = (int)nfree;
+        g.ftop[1] = 0;
+    }
+}
+
+void Launcher::slots_full(long long ntot)
+{
+    pdl_launch(k_slots_full, blocks_dense(ntot), NTHREADS, 0, st, g, ntot);
+    ++n;
+}
+
+// Refinement flags over cells [from, to), added into *out: after the
+// closure of an adaptation at level la every flagged cell of levels
+// la..L-1 owns 2^d nodes of the new tree.
+__global__ void k_count_ref(const __grid_constant__ Grid g, long long from, long long to, int* out)
+{
+    MRLT_ENTER(g);
+    int c = 0;
+    GRID_STRIDE(i, to - from) c += (g.flag[from + i] & FL_REF) ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+void Launcher::count_refined(int la, int* out)
+{
+    cudaMemsetAsync(out, 0, sizeof(int), st);
+    const long long from = g.off[la], to = g.off[g.L];
+    pdl_launch(k_count_ref, blocks_dense(to - from), NTHREADS, 0, st, g, from, to, out);
+    ++n;
+}
+
+// Does the tree flagged by the remesh at level la of fine iteration it fit
+// the node arrays?  The blocks count the refinement flags of levels
+// la..L-1 into room[0]; the new tree has 2^d nodes above level la per flag,
+// and the slots it may take are the free ones plus those of the nodes above
+// level la now (the remesh releases them first).  The last block to finish
+// (ticket room[3]) decides: short of slots, the solver halts at this
+// iteration, room[1] = it + 1, room[2] = the nodes of the new tree.
+__global__ void k_room(const __grid_constant__ Grid g, int la, long long it)
+{
+    MRLT_ENTER(g);
+    __shared__ int blk;
+    if (threadIdx.x == 0) blk = 0;
+    __syncthreads();
+    const long long from = g.off[la], to = g.off[g.L];
+    int c = 0;
+    GRID_STRIDE(i, to - from) c += (g.flag[from + i] & FL_REF) ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&blk, c);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (blk) atomicAdd(&g.room[0], blk);
+    __threadfence();
+    if (atomicAdd(&g.room[3], 1) != (int)gridDim.x - 1) return;
+    __threadfence();
+    const long long fresh = (long long)atomicExch(&g.room[0], 0) << g.d;
+    g.room[3] = 0;
+    long long above = 0, below = 0;
+    for (int l = g.lb; l <= g.L; ++l) {
+        const long long n = (long long)g.counts[l] + g.counts[LMAX + 1 + l];
+        if (l > la) above += n;
+        else below += n;
+    }
+    if (fresh > g.ftop[0] + above) {
+        g.room[2] = (int)(below + fresh);
+        g.room[1] = (int)(it + 1);
+    }
+}
+
+void Launcher::check_room(int la, long long it)
+{
+    pdl_launch(k_room, blocks_dense(g.off[g.L] - g.off[la]), NTHREADS, 0, st, g, la, it);
+    ++n;
+}
+
+// adaptation flags of cells [from, to) cleared
+__global__ void k_clear_flags(const __grid_constant__ Grid g, long long from, long long to)
+{
+    MRLT_ENTER(g);
+    dev_clear_flags(g, from, to);
+}
+
+void Launcher::clear_flags(long long from, long long to)
+{
+    pdl_launch(k_clear_flags, blocks_dense(to - from), NTHREADS, 0, st, g, from, to);
+    ++n;
+}
+
+// Compacting copy into node arrays of a new capacity: the nodes of level l
+// (leaves, then internal nodes, in list order) take the consecutive slots
+// from base[l] + 1; their fields and registers are copied from the old
+// arrays (`from`), the slot map rewritten.  The free stack of the new arrays
+// holds every slot above the nodes.
+template <class T>
+__global__ void k_renumber(Grid g, Grid from, LevelChunks base, long long used)
+{
+    pdl_enter();
+    for (int l = g.lb; l <= g.L; ++l) {
+        const long long N = g.N[l];
+        const int nl = g.counts[l], ni = g.counts[LMAX + 1 + l];
+        GRID_STRIDE(t, nl + ni)
+        {
+            const long long id = t < nl ? g.leaves[g.off[l] + t] : g.inner[g.off[l] + t - nl];
+            if (id < 0 || id >= N) {
+                atomicOr(g.err, ERR_INDEX);
+                continue;
+            }
+            const int os = slot_of(from, l, id), ns = (int)(1 + base.base[l] + t);
+            for (int f = 0; f < NFIELD; ++f) {
+                const T* a = nd<T>(from, f, os);
+                T* b = nd<T>(g, f, ns);
+                for (int v = 0; v < g.m; ++v) b[v] = a[v];
+            }
+            if (g.rg) {
+                const double* a = regs(from.rg, from, os);
+                double* b = regs(g.rg, g, ns);
+                for (int r = 0; r < g.nf * g.m; ++r) b[r] = a[r];
+            }
+            g.slot[g.off[l] + id] = ns;
+        }
+    }
+    const long long nfree = g.cap - 1 - used;
+    GRID_STRIDE(k, nfree) g.fstack[k] = (int)(g.cap - 1 - k);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g.ftop[0] = (int)nfree;
+        g.ftop[1] = 0;
+    }
+}
+
+void Launcher::renumber(const Grid& from, const int* counts_host, long long used)
+{
+    LevelChunks base;
+    base.lo = g.lb;
+    base.hi = g.L;
+    int acc = 0;
+    for (int l = g.lb; l <= g.L; ++l) {
+        base.base[l] = acc;
+        acc += counts_host[l] + counts_host[LMAX + 1 + l];
+    }
+    base.base[g.L + 1] = acc;
+    long long cnt = used > g.cap - 1 - used ? used : g.cap - 1 - used;
+    if (g.prec) pdl_launch(k_renumber<float>, blocks_dense(cnt), NTHREADS, 0, st, g, from, base, used);
+    else pdl_launch(k_renumber<double>, blocks_dense(cnt), NTHREADS, 0, st, g, from, base, used);
     ++n;
 }
 

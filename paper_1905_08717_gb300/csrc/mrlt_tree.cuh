@@ -22,7 +22,13 @@ struct Launcher {
     void scale_init();                                 // running max |q_v| := 1e-14
     void set_dt(double dt);                            // *g.dtp := dt
     void set_leaves(const int* keys, const double* vals, long long count); // leaf q^n and end values
-    void store_finest(const double* src); // finest-level q^n from double data (float fields)
+    void store_finest(const double* src); // finest-level q^n from double data [v][cell]
+    void slots_full(long long ntot);      // every cell of every level a node (a new solver's tree)
+    // compacting copy of the nodes from `from` into the arrays of g (a new capacity)
+    void renumber(const Grid& from, const int* counts_host, long long used);
+    void count_refined(int la, int* out);   // *out = refinement flags of levels la..L-1
+    void check_room(int la, long long it);  // halt unless the flagged tree fits (k_room)
+    void clear_flags(long long from, long long to);
     void finite(int l);
     void mass(int l, double* part);
     void pack(int l, long long base, int* keys, double* vals);

@@ -26,8 +26,6 @@ __device__ __forceinline__ void dev_leaf_copy(const Grid& g, int lo, int hi, int
         const int cnt = g.counts[l];
         const int* list = g.leaves + g.off[l];
         const long long N = g.N[l];
-        const T* a = fld<T>(g, from, l);
-        T* b = fld<T>(g, to, l);
         MRLT_GRID_STRIDE(t, cnt)
         {
             const long long id = list[t];
@@ -35,7 +33,10 @@ __device__ __forceinline__ void dev_leaf_copy(const Grid& g, int lo, int hi, int
                 atomicOr(g.err, ERR_INDEX);
                 continue;
             }
-            for (int v = 0; v < g.m; ++v) b[v * N + id] = a[v * N + id];
+            const int sl = slot_of(g, l, id);
+            const T* a = nd<T>(g, from, sl);
+            T* b = nd<T>(g, to, sl);
+            for (int v = 0; v < g.m; ++v) b[v] = a[v];
         }
     }
 }
@@ -54,7 +55,7 @@ __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
 {
     const int cnt = g.counts[LMAX + 1 + l];
     const int* list = g.inner + g.off[l];
-    const long long N = g.N[l], Nc = g.N[l + 1];
+    const long long N = g.N[l];
     constexpr int NCH = 1 << D;
     MRLT_GRID_STRIDE(t, cnt)
     {
@@ -65,28 +66,30 @@ __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
         }
         int c[3];
         cell_xyz(g, l, id, c);
-        long long ch[NCH];
+        int csl[NCH];
         uint8_t cst[NCH];
 #pragma unroll
         for (int k = 0; k < NCH; ++k) {
-            ch[k] = cell_id(g, l + 1, 2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
-                            D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
-            cst[k] = status(g, l + 1, ch[k]);
+            const long long ch = cell_id(g, l + 1, 2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
+                                         D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
+            cst[k] = status(g, l + 1, ch);
+            csl[k] = slot_of(g, l + 1, ch);
         }
-        const T* c0 = fld<T>(g, F_Q0, l + 1);
-        const T* c1 = fld<T>(g, F_Q1, l + 1);
-        const T* c2 = fld<T>(g, F_Q2, l + 1);
-        const T* ce = fld<T>(g, F_QE, l + 1);
-        T* q0 = fld<T>(g, F_Q0, l);
-        T* q1 = fld<T>(g, F_Q1, l);
-        T* q2 = fld<T>(g, F_Q2, l);
-        T* qe = fld<T>(g, F_QE, l);
+        const int sl = slot_of(g, l, id);
+        T* q0 = nd<T>(g, F_Q0, sl);
+        T* q1 = nd<T>(g, F_Q1, sl);
+        T* q2 = nd<T>(g, F_Q2, sl);
+        T* qe = nd<T>(g, F_QE, sl);
         for (int v = 0; v < g.m; ++v) {
-            const long long o = v * N + id;
+            const int o = v;
             T acc = T(0);
 #pragma unroll
             for (int k = 0; k < NCH; ++k) {
-                const long long oc = v * Nc + ch[k];
+                const T* c0 = nd<T>(g, F_Q0, csl[k]);
+                const T* c1 = nd<T>(g, F_Q1, csl[k]);
+                const T* c2 = nd<T>(g, F_Q2, csl[k]);
+                const T* ce = nd<T>(g, F_QE, csl[k]);
+                const int oc = v;
                 T w;
                 switch (mode) {
                 case PM_Q0: w = c0[oc]; break;
@@ -107,12 +110,12 @@ __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
             case PM_Q1: case PM_PRJ2: q1[o] = mean; break;
             case PM_Q2: q2[o] = mean; break;
             case PM_REF2:
-                fld<T>(g, F_XH, l)[o] = mean;
+                nd<T>(g, F_XH, sl)[o] = mean;
                 q1[o] = T(2) * mean - q0[o];
                 break;
             case PM_REF3: {
-                fld<T>(g, F_N1, l)[o] = mean;
-                fld<T>(g, F_N3, l)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * mean;
+                nd<T>(g, F_N1, sl)[o] = mean;
+                nd<T>(g, F_N3, sl)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * mean;
                 q2[o] = T(-5.5) * q0[o] - T(1.5) * q1[o] + T(8) * mean;
                 break;
             }
@@ -122,14 +125,14 @@ __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
                 break;
             default: { // PM_MID
                 if (g.rk == 2) {
-                    fld<T>(g, F_NH, l)[o] = mean;
+                    nd<T>(g, F_NH, sl)[o] = mean;
                     qe[o] = T(-2) * q0[o] - q1[o] + T(4) * mean;
                 } else {
                     q2[o] = mean;
                     qe[o] = T(2) * mean - q0[o];
                     const T n1 = (mean + T(5.5) * q0[o] + T(1.5) * q1[o]) * T(0.125);
-                    fld<T>(g, F_N1, l)[o] = n1;
-                    fld<T>(g, F_N3, l)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * n1;
+                    nd<T>(g, F_N1, sl)[o] = n1;
+                    nd<T>(g, F_N3, sl)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * n1;
                 }
             }
             }
@@ -156,7 +159,7 @@ __device__ __forceinline__ void dev_detail(const Grid& g, int lo, int hi)
     for (int l = lo; l <= hi; ++l) {
         const int cnt = g.counts[LMAX + 1 + l];
         const int* list = g.inner + g.off[l];
-        const long long N = g.N[l], Nc = g.N[l + 1];
+        const long long N = g.N[l];
         const double el = eps_level(g, l + 1);
         MRLT_GRID_STRIDE(t, cnt)
         {
@@ -179,9 +182,9 @@ __device__ __forceinline__ void dev_detail(const Grid& g, int lo, int hi)
                 for (int k = 0; k < (1 << D); ++k) {
                     const long long cid = cell_id(g, l + 1, 2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
                                                   D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
-                    const T* qc = fld<T>(g, F_Q0, l + 1) + cid;
+                    const T* qc = nd<T>(g, F_Q0, slot_of(g, l + 1, cid));
 #pragma unroll
-                    for (int v = 0; v < M; ++v) nrm = fmax(nrm, fabs(double(qc[v * Nc]) - p[k][v]) / sc[v]);
+                    for (int v = 0; v < M; ++v) nrm = fmax(nrm, fabs(double(qc[v]) - p[k][v]) / sc[v]);
                 }
                 if (fabs(nrm - el) <= 1e-10 * el || fabs(nrm - 8.0 * el) <= 8e-10 * el)
                     atomicAdd(g.near, 1ull);
@@ -325,14 +328,45 @@ __device__ __forceinline__ void dev_close(const Grid& g, int l)
     }
 }
 
+// Slots of the nodes a remesh removes (levels la+1..L: a node whose parent
+// is not refined any more), pushed on the free stack before the apply passes
+// pop slots for new nodes.  Walks the node lists of the tree being replaced.
+static __device__ __forceinline__ void dev_release(const Grid& g, int la)
+{
+    for (int l = la + 1; l <= g.L; ++l) {
+        const long long N = g.N[l];
+        for (int which = 0; which < 2; ++which) {
+            const int cnt = g.counts[which * (LMAX + 1) + l];
+            const int* list = (which ? g.inner : g.leaves) + g.off[l];
+            MRLT_GRID_STRIDE(t, cnt)
+            {
+                const long long id = list[t];
+                if (id < 0 || id >= N) {
+                    atomicOr(g.err, ERR_INDEX);
+                    continue;
+                }
+                int c[3];
+                cell_xyz(g, l, id, c);
+                const long long p = cell_id(g, l - 1, c[0] >> 1, c[1] >> 1, c[2] >> 1);
+                if (g.flag[g.off[l - 1] + p] & FL_REF) continue; // stays
+                const int sl = slot_of(g, l, id);
+                if (sl > 0) g.fstack[atomicAdd(&g.ftop[0], 1)] = sl;
+                g.slot[g.off[l] + id] = -1;
+            }
+        }
+    }
+}
+
 // install the new tree on level l (top-down): status from the refinement
-// flags; new nodes predicted from level l-1 (Sec. 2, in FP64, stored as T);
+// flags; new nodes take a free slot (the sink, with ERR_CAPACITY, when none
+// is left) and are predicted from level l-1 (Sec. 2, in FP64, stored as T);
 // new leaves and merged nodes get q^{n+1} = q^n; registers of changed nodes
 // cleared
 template <int D, int M, class T>
 __device__ __forceinline__ void dev_apply(const Grid& g, int l, int la)
 {
     const long long N = g.N[l];
+    const int top = g.ftop[0]; // free slots after this remesh's releases
     MRLT_GRID_STRIDE(id, N)
     {
         const uint8_t old = status(g, l, id);
@@ -349,25 +383,32 @@ __device__ __forceinline__ void dev_apply(const Grid& g, int l, int la)
         const uint8_t nw = exists ? (refined ? 2 : 1) : 0;
         if (nw == old) continue;
         g.st[g.off[l] + id] = nw;
-        T* q0 = fld<T>(g, F_Q0, l) + id;
-        if (old == 0 && nw != 0) {
+        if (nw == 0) continue; // removed: its slot was released before the apply passes
+        int sl;
+        if (old == 0) {
+            const int k = atomicAdd(&g.ftop[1], 1);
+            sl = k < top ? g.fstack[top - 1 - k] : 0;
+            if (k >= top) atomicOr(g.err, ERR_CAPACITY);
+            g.slot[g.off[l] + id] = sl;
+        } else {
+            sl = slot_of(g, l, id);
+        }
+        T* q0 = nd<T>(g, F_Q0, sl);
+        if (old == 0) {
             const Ctx x{l, 0, g.lb};
             double p[M];
             predict<D, M, T, double>(g, x, l, c, p);
 #pragma unroll
-            for (int v = 0; v < M; ++v) q0[v * N] = T(p[v]);
+            for (int v = 0; v < M; ++v) q0[v] = T(p[v]);
         }
         if (nw == 1) {
-            T* qe = fld<T>(g, F_QE, l) + id;
+            T* qe = nd<T>(g, F_QE, sl);
 #pragma unroll
-            for (int v = 0; v < M; ++v) qe[v * N] = q0[v * N];
+            for (int v = 0; v < M; ++v) qe[v] = q0[v];
         }
-        if (g.rc) {
-            const long long roff = g.off[l] * g.nf * M;
-            for (int r = 0; r < g.nf * M; ++r) {
-                g.rc[roff + r * N + id] = 0.0;
-                g.rf[roff + r * N + id] = 0.0;
-            }
+        if (g.rg) {
+            double* rg = regs(g.rg, g, sl);
+            for (int r = 0; r < g.nf * M; ++r) rg[r] = 0.0;
         }
     }
 }
@@ -419,6 +460,11 @@ __device__ __forceinline__ void chunk_count(const Grid& g, const LevelChunks& lc
         }
         bc[2 * chunk] = a;
         bc[2 * chunk + 1] = b;
+        if (chunk == 0) { // the slots popped by the remesh leave the free stack
+            const int k = g.ftop[1], top = g.ftop[0];
+            g.ftop[0] = top - (k < top ? k : top);
+            g.ftop[1] = 0;
+        }
     }
     __syncthreads();
 }
@@ -546,7 +592,7 @@ __device__ __forceinline__ void dev_reflux(const Grid& g, int lo, int hi)
     for (int l = lo; l <= hi; ++l) {
         const int cnt = g.counts[l];
         const int* list = g.leaves + g.off[l];
-        const long long N = g.N[l], Nf = g.N[l + 1];
+        const long long N = g.N[l];
         const int m = g.m;
         constexpr int NT = 1 << (D - 1);
         MRLT_GRID_STRIDE(t, cnt)
@@ -578,20 +624,22 @@ __device__ __forceinline__ void dev_reflux(const Grid& g, int lo, int hi)
                     ch[tt] = cell_id(g, l + 1, p[0], p[1], p[2]);
                     if (status(g, l + 1, ch[tt]) != 1) atomicOr(g.err, ERR_REFLUX);
                 }
-                double* rc = g.rc + g.off[l] * g.nf * m + id;
-                double* rf = g.rf + g.off[l + 1] * g.nf * m;
-                T* qe = fld<T>(g, F_QE, l) + id;
+                const int sl = slot_of(g, l, id);
+                double* rc = regs(g.rg, g, sl);
+                int csl[NT];
+                for (int tt = 0; tt < NT; ++tt) csl[tt] = slot_of(g, l + 1, ch[tt]);
+                T* qe = nd<T>(g, F_QE, sl);
                 const double idx = 1.0 / g.dx[l][k];
                 for (int v = 0; v < m; ++v) {
                     double sum = 0.0;
                     for (int tt = 0; tt < NT; ++tt) {
-                        double* r = rf + (long long)(opp * m + v) * Nf + ch[tt];
+                        double* r = regs(g.rg, g, csl[tt]) + opp * m + v;
                         sum += *r;
                         *r = 0.0;
                     }
-                    double* r = rc + (long long)(fi * m + v) * N;
+                    double* r = rc + fi * m + v;
                     // the correction from the FP64 registers, rounded to T once
-                    qe[v * N] = T(double(qe[v * N]) + side * (*r - sum * (1.0 / NT)) * idx);
+                    qe[v] = T(double(qe[v]) + side * (*r - sum * (1.0 / NT)) * idx);
                     *r = 0.0;
                 }
             }
@@ -613,7 +661,8 @@ __device__ __forceinline__ void dev_scale(const Grid& g, int lo, int hi)
         {
             const long long id = list[t];
             if (id < 0 || id >= N) continue;
-            for (int v = 0; v < g.m; ++v) mx[v] = fmax(mx[v], fabs(double(fld<T>(g, F_Q0, l)[v * N + id])));
+            const T* q0 = nd<T>(g, F_Q0, slot_of(g, l, id));
+            for (int v = 0; v < g.m; ++v) mx[v] = fmax(mx[v], fabs(double(q0[v])));
         }
         for (int v = 0; v < g.m; ++v) {
             double a = mx[v];
@@ -636,8 +685,9 @@ __device__ __forceinline__ void dev_finite(const Grid& g, int lo, int hi)
         {
             const long long id = list[t];
             if (id < 0 || id >= N) continue;
+            const T* qe = nd<T>(g, F_QE, slot_of(g, l, id));
             for (int v = 0; v < g.m; ++v)
-                if (!isfinite(double(fld<T>(g, F_QE, l)[v * N + id]))) atomicOr(g.err, ERR_NONFINITE);
+                if (!isfinite(double(qe[v]))) atomicOr(g.err, ERR_NONFINITE);
         }
     }
 }
@@ -657,10 +707,10 @@ __device__ __forceinline__ void dev_wave(const Grid& g, int lo, int hi)
         {
             const long long id = list[t];
             if (id < 0 || id >= N) continue;
-            const T* qe = fld<T>(g, F_QE, l) + id;
+            const T* qe = nd<T>(g, F_QE, slot_of(g, l, id));
             double q[M];
 #pragma unroll
-            for (int v = 0; v < M; ++v) q[v] = double(qe[v * N]);
+            for (int v = 0; v < M; ++v) q[v] = double(qe[v]);
             const double s = wave_speed<EQ, D, M>(g, q);
             w = fmax(w, s != s ? 1e300 : s);
         }

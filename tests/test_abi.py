@@ -112,7 +112,7 @@ def test_null_handles_and_arguments(lib):
     for name, args in [("mr_reset", (None, None)), ("mr_set_tree", (None, None)), ("mr_adapt", (None,)),
                        ("mr_set_async", (None, 1)), ("mr_sync", (None,)), ("mr_profile", (None, 1)),
                        ("mr_set_grid_cap", (None, 0)), ("mr_batch_set_grid_cap", (None, 0)),
-                       ("mr_set_launch_mode", (None, 0)), ("mr_selftest_grid_wait", (0, 0, ctypes.c_double(1.0), None)),
+                       ("mr_set_launch_mode", (None, 0)), ("mr_reserve_nodes", (None, ctypes.c_longlong(8))), ("mr_selftest_grid_wait", (0, 0, ctypes.c_double(1.0), None)),
                        ("mr_server_set_grid_cap", (None, 0)), ("mr_server_advance", (None, None, None)),
                        ("mr_server_status", (None, ctypes.c_longlong(1))),
                        ("mr_server_release", (None, ctypes.c_longlong(1)))]:

@@ -69,9 +69,21 @@ def test_reference_arm_runs_on_rank_zero_only():
 
 def test_traffic_figure_comes_from_the_committed_dram_summary():
     """roofline.traffic is the committed per-leaf-stage DRAM figure times the
-    leaf-stages of one launch; the summary must parse to a positive number
-    below the algorithmic bytes of a leaf-stage (the state is L2-resident)."""
+    leaf-stages of one launch, and only while the summary's kernel_sha16 line
+    names the stage-kernel sources built here (null otherwise); the figure
+    parses to a positive number below the algorithmic bytes of a leaf-stage
+    (the state is L2-resident)."""
     sys.path.insert(0, ROOT)
     import bench
+    val, sha = None, None
+    for ln in open(os.path.join(ROOT, "profiles", "stage_kernel_dram_euler2d_L10.md")):
+        if ln.startswith("dram_bytes_per_leaf_stage:"):
+            val = float(ln.split(":")[1].split()[0])
+        elif ln.startswith("kernel_sha16:"):
+            sha = ln.split(":")[1].strip()
+    assert val is not None and 0.0 < val < max(bench.BYTES_PER_LEAF_STAGE.values())
     tpl = bench._traffic_per_leaf_stage()
-    assert tpl is not None and 0.0 < tpl < max(bench.BYTES_PER_LEAF_STAGE.values())
+    if sha == bench.stage_kernel_hash():
+        assert tpl == val
+    else:
+        assert tpl is None
