@@ -102,13 +102,13 @@ typedef struct mr_config {
  * only for the nodes of the tree, in node arrays.  A new tree keeps room for
  * every cell until the first macro-step boundary.  From there on (unless the
  * full arrays take at most 32 MB, or the launch mode is MR_LAUNCH_PERSISTENT)
- * the arrays hold 1.5 to 3 times the nodes in use: at each macro-step
+ * the arrays hold 1.25 to 2 times the nodes in use: at each macro-step
  * boundary the first remesh of the macro step is flagged and counted before
  * its tree is installed, and the arrays are resized to fit that tree with a
  * margin; a remesh inside a macro step that would not fit halts the
- * solver's device work, and the host grows the arrays and resumes at that
- * remesh (checked every 16 fine iterations), so a growing tree never fails
- * a step while device memory lasts.  Results do not depend on the capacity.
+ * solver's device work, and at the end of the macro step the host grows the
+ * arrays and resumes at that remesh, so a growing tree never fails a step
+ * while device memory lasts.  Results do not depend on the capacity.
  * Returns MR_E_INVALID for a bad configuration, MR_E_NOMEM when device memory
  * is insufficient: the footprint of the full tree is compared with the free
  * device memory before anything is allocated or q0 is read.  *out receives
@@ -348,8 +348,9 @@ void mr_batch_destroy(mr_batch* b);
  * per-cell arrays plus node arrays for a projected node count, which models an
  * adapted tree as fronts of codimension one, min(all cells, 64 x 2^{(d-1) L})
  * nodes with the compact margin of mr_create; once created, the request counts
- * the larger of that and its actual footprint.  Results stay on the device
- * until released. */
+ * the larger of that and its actual footprint, which is the full tree until
+ * its first macro-step boundary and compact from there on.  Results stay on
+ * the device until released. */
 typedef struct mr_server mr_server;
 
 /* mem_budget_bytes: device bytes all admitted problems may hold together;

@@ -29,7 +29,6 @@ struct mr_solver {
     int* h_top = nullptr;           // pinned: [0] free slots, [1] refinement flags of a head,
                                     // [2..3] halt record (Grid::room[1..2])
     int* d_nref = nullptr;          // device: refinement flags counted by a head
-    long long used_prev = 0;        // nodes in use at the previous capacity check
     long long used_macro = 0;       // nodes of the tree installed at the macro step's start
     long long grow_macro = 0;       // largest growth past used_macro seen in this macro step
     // head of a macro step: iteration 0 up to the flags of its new tree (and
@@ -66,10 +65,6 @@ struct mr_solver {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t macro_exec = nullptr;
     long long macro_launches = 0, macro_stage_launches = 0;
-    // pieces of a macro step between capacity checks (compact node arrays):
-    // graphs of kPiece iterations, one per position in the macro step
-    std::vector<cudaGraphExec_t> piece_exec;
-    std::vector<long long> piece_launches, piece_stage_launches;
     bool graph_off = false; // capture failed once, or disabled by the caller
     // batched use: the macro-step finiteness check copies the device error
     // bits here (pinned host memory) instead of synchronising
@@ -218,16 +213,12 @@ mr_status dev_alloc(mr_solver* h, T** p, size_t count)
 // need + 2 margin.  Inside a macro step (adaptation at every fine iteration,
 // on the levels that are active) every remesh first checks on the device
 // that its tree fits, and halts the solver's device work if it does not
-// (k_room).  The host reads the free-slot count and the halt record at check
-// points every kPiece fine iterations (a macro step runs in pieces of kPiece
-// iterations, each its own CUDA graph) and at the end of a macro step: after
-// a halt it grows the arrays to the flagged tree plus two margins of a
-// quarter of it and resumes at the halted remesh; otherwise, with margin =
-// max(2 x the nodes added since the last check, a quarter of the nodes in
-// use, kMinSlots), fewer than margin free slots grow the arrays to used + 2
-// margin.  Reservations made with mr_reserve_nodes are a floor.
+// (k_room).  The host reads the halt record at the end of the macro step (a
+// solver that waits) or with the CFL speed at the next boundary (batch and
+// server instances); after a halt it grows the arrays to the flagged tree
+// plus two margins of a quarter of it and resumes at the halted remesh.
+// Reservations made with mr_reserve_nodes are a floor.
 constexpr long long kMinSlots = 4096;
-constexpr long long kPiece = 16;
 constexpr size_t kDenseBytes = 32u << 20;
 
 size_t per_node_bytes(const Grid& g, bool reg)
@@ -292,7 +283,7 @@ mr_status set_capacity(mr_solver* h, long long newcap, bool keep)
         for (int l = g.lb; l <= g.L; ++l) used += cnt[l] + cnt[LMAX + 1 + l];
         if (used + 1 > newcap) newcap = used + 1;
     }
-    if (h->macro_exec || h->head_exec || !h->piece_exec.empty()) { // captured with the old arrays
+    if (h->macro_exec || h->head_exec) { // captured with the old arrays
         MR_CK(cudaStreamSynchronize(h->stream));
         drop_graphs(h);
     }
@@ -328,10 +319,10 @@ bool can_halt(const mr_solver* h)
     return split_head(h) && h->cfg.adapt_mode == MR_ADAPT_EVERY;
 }
 
-// The capacity rule at a check point, with the free-slot count `top` read
-// back: a macro-step boundary (next = nodes of the tree its head flagged, or
-// -1 when the tree does not change there) or a check between pieces.
-mr_status adjust_capacity(mr_solver* h, int top, bool boundary, long long next = -1)
+// The capacity rule at a macro-step boundary, with the free-slot count `top`
+// read back; next = nodes of the tree its head flagged, or -1 when the tree
+// does not change there.
+mr_status adjust_capacity(mr_solver* h, int top, long long next = -1)
 {
     if ((small_problem(h) || h->launch_mode == MR_LAUNCH_PERSISTENT) && dense_capacity(h)) return MR_OK;
     const long long cap = h->K.g.cap, used = cap - 1 - top;
@@ -341,21 +332,12 @@ mr_status adjust_capacity(mr_solver* h, int top, bool boundary, long long next =
     };
     auto at_least = [](long long a, long long b) { return a > b ? a : b; };
     if (used - h->used_macro > h->grow_macro) h->grow_macro = used - h->used_macro;
-    if (boundary) {
-        const long long need = at_least(used, next);
-        const long long margin = at_least(at_least(h->grow_macro, need / 4), kMinSlots);
-        const long long target = clamp(need + 2 * margin + 1);
-        h->used_prev = h->used_macro = next >= 0 ? next : used;
-        h->grow_macro = 0;
-        if (cap - 1 < need + margin || cap - 1 > need + 4 * margin) return set_capacity(h, target, true);
-        return MR_OK;
-    }
-    if (dense_capacity(h)) return MR_OK;
-    const long long added = used > h->used_prev ? used - h->used_prev : 0;
-    h->used_prev = used;
-    const long long margin = at_least(at_least(2 * added, used / 4), kMinSlots);
-    const long long target = clamp(used + 2 * margin + 1);
-    if (top < margin && cap < target) return set_capacity(h, target, true);
+    const long long need = at_least(used, next);
+    const long long margin = at_least(at_least(h->grow_macro, need / 4), kMinSlots);
+    const long long target = clamp(need + 2 * margin + 1);
+    h->used_macro = next >= 0 ? next : used;
+    h->grow_macro = 0;
+    if (cap - 1 < need + margin || cap - 1 > need + 4 * margin) return set_capacity(h, target, true);
     return MR_OK;
 }
 
@@ -376,33 +358,38 @@ mr_status fit_new_tree(mr_solver* h)
 {
     long long used = 0;
     MR_TRY(count_nodes(h, &used));
-    h->used_prev = h->used_macro = used;
+    h->used_macro = used;
     h->grow_macro = 0;
     h->head_pending = h->head_done = false;
     return MR_OK;
 }
 
-// A check point inside a macro step: the free-slot count and the halt
-// record read back (synchronising).  After a halt at iteration p the arrays
-// grow to hold the flagged tree and two margins of a quarter of it, the
-// halt is cleared and the position rewinds to p: the caller resumes with the
+// a batch or server instance: its progress is driven by events, not waits
+bool is_instance(const mr_solver* h) { return h->async_err && h->async_err != h->own_err; }
+
+// Recovery from a halt whose record (h_top[2..3]) and free-slot count
+// (h_top[0]) were read back with the stream idle: the halt at iteration p
+// is cleared, the arrays grow to hold the flagged tree and two margins of a
+// quarter of it, and the position rewinds to p (into the macro step just
+// counted complete, when pos is 0).  The caller then resumes with the
 // installation of p's tree (its flags are intact: nothing ran after them)
-// and launches the iterations after p again.  Otherwise the capacity rule.
-mr_status check_point(mr_solver* h, bool* rewound)
+// and launches the iterations after p again (h->redo, not counted twice).
+mr_status recover(mr_solver* h)
 {
     Grid& g = h->K.g;
-    *rewound = false;
-    MR_CK(cudaMemcpyAsync(h->h_top, g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    MR_CK(cudaMemcpyAsync(h->h_top + 2, g.room + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    MR_CK(cudaStreamSynchronize(h->stream));
-    if (!h->h_top[2]) return adjust_capacity(h, h->h_top[0], false);
+    const long long nit = 1LL << (g.L - g.lb);
     const long long p = h->h_top[2] - 1, tree = h->h_top[3];
-    if (p < 1 || p >= h->pos) {
+    const long long launched = h->pos == 0 ? nit : h->pos;
+    if (p < 1 || p >= launched) {
         h->err = "halt record out of range";
         return MR_E_STATE;
     }
     MR_CK(cudaMemsetAsync(g.room, 0, 4 * sizeof(int), h->stream));
     h->h_top[2] = h->h_top[3] = 0;
+    if (h->pos == 0) {
+        --h->macros;
+        h->head_pending = h->head_done = false; // the boundary's head ran halted: again
+    }
     const long long used = g.cap - 1 - h->h_top[0];
     const long long need = tree > used ? tree : used;
     long long margin = need / 4;
@@ -410,23 +397,36 @@ mr_status check_point(mr_solver* h, bool* rewound)
     long long target = need + 2 * margin + 1;
     if (target < h->reserved + 1) target = h->reserved + 1;
     MR_TRY(set_capacity(h, target, true));
-    h->used_prev = need;
     if (need - h->used_macro > h->grow_macro) h->grow_macro = need - h->used_macro;
-    h->redo += h->pos - p;
+    h->redo += launched - p;
     h->pos = p;
     h->resume = true;
     ++h->halts;
+    return MR_OK;
+}
+
+// the free-slot count and the halt record on their way to h_top
+mr_status enqueue_slot_record(mr_solver* h)
+{
+    MR_CK(cudaMemcpyAsync(h->h_top, h->K.g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MR_CK(cudaMemcpyAsync(h->h_top + 2, h->K.g.room + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    return MR_OK;
+}
+
+// A check point at the end of a macro step or call (synchronising): after
+// a halt the position rewinds (*rewound).
+mr_status check_point(mr_solver* h, bool* rewound)
+{
+    *rewound = false;
+    MR_TRY(enqueue_slot_record(h));
+    MR_CK(cudaStreamSynchronize(h->stream));
+    if (!h->h_top[2]) return MR_OK;
+    MR_TRY(recover(h));
     *rewound = true;
     return MR_OK;
 }
 
-// fine iterations between capacity checks inside a macro step (only
-// adaptation at every fine iteration changes the tree there)
-long long piece_len(const mr_solver* h, long long nit)
-{
-    if (dense_capacity(h) || nit <= kPiece || h->cfg.adapt_mode != MR_ADAPT_EVERY) return nit;
-    return kPiece;
-}
+mr_status run_iters(mr_solver* h, double dt, long long n);
 
 void drop_graphs(mr_solver* h)
 {
@@ -434,11 +434,6 @@ void drop_graphs(mr_solver* h)
     h->macro_exec = nullptr;
     if (h->head_exec) cudaGraphExecDestroy(h->head_exec);
     h->head_exec = nullptr;
-    for (cudaGraphExec_t e : h->piece_exec)
-        if (e) cudaGraphExecDestroy(e);
-    h->piece_exec.clear();
-    h->piece_launches.clear();
-    h->piece_stage_launches.clear();
 }
 
 // transient device scratch from the pool, released in stream order
@@ -719,20 +714,24 @@ mr_status head_enqueue(mr_solver* h)
 // head (if any) and the free-slot read enqueued before it
 mr_status head_finish(mr_solver* h)
 {
-    if (!h->head_pending) return adjust_capacity(h, h->h_top[0], true);
+    if (!h->head_pending) return adjust_capacity(h, h->h_top[0]);
     h->head_pending = false;
     h->head_done = true;
     const Grid& g = h->K.g;
     const long long next = g.N[g.lb] + ((long long)h->h_top[1] << g.d);
-    return adjust_capacity(h, h->h_top[0], true, next);
+    return adjust_capacity(h, h->h_top[0], next);
 }
 
 // head and capacity rule of a macro-step boundary, synchronously
 mr_status boundary_check(mr_solver* h)
 {
     MR_TRY(head_enqueue(h));
-    MR_CK(cudaMemcpyAsync(h->h_top, h->K.g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MR_TRY(enqueue_slot_record(h));
     MR_TRY(sync_check(h));
+    if (h->h_top[2]) { // check points end every macro step of a solver that waits
+        h->err = "halt pending at a macro-step boundary";
+        return MR_E_STATE;
+    }
     return head_finish(h);
 }
 
@@ -817,14 +816,14 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
         i += fresh;
         h->pos += k;
         h->head_done = h->resume = false;
-        h->unchecked = can_halt(h) && !dense_capacity(h);
+        // batch and server instances learn of a halt at their next boundary
+        h->unchecked = can_halt(h) && !dense_capacity(h) && !is_instance(h);
     };
     for (;;) {
         const bool done = i >= n && h->redo == 0;
-        // check points: every kPiece fine iterations, the end of a macro
-        // step and the end of this call (compact arrays, remeshes at every
-        // fine iteration)
-        if (h->unchecked && (h->pos % kPiece == 0 || h->pos == nit || done)) {
+        // check points: the end of a macro step and the end of this call
+        // (compact arrays, remeshes at every fine iteration)
+        if (h->unchecked && (h->pos == nit || done)) {
             h->unchecked = false;
             bool rewound = false;
             MR_TRY(check_point(h, &rewound));
@@ -856,7 +855,6 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
             advance(1);
             continue;
         }
-        const long long piece = piece_len(h, nit);
         const long long left = n - i + h->redo; // iterations still to launch
         if (h->launch_mode == MR_LAUNCH_PERSISTENT) {
             long long chunk = left < nit - h->pos ? left : nit - h->pos;
@@ -867,7 +865,7 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
         }
         h->wmax_valid = false;
         const bool can_graph = !h->prof && !h->graph_off && nit <= kMaxGraphIters;
-        if (can_graph && piece == nit && h->pos == 0 && left >= nit) { // a whole macro step
+        if (can_graph && h->pos == 0 && left >= nit) { // a whole macro step
             if (!h->macro_exec && !capture_macro(h, nit)) {
                 h->graph_off = true; // launch directly from now on
                 continue;
@@ -876,24 +874,6 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
             h->K.n += h->macro_launches;
             h->stage_launches += h->macro_stage_launches;
             advance(nit);
-            continue;
-        }
-        if (can_graph && piece < nit && h->pos % piece == 0 && left >= piece) { // a piece of one
-            const size_t k = (size_t)(h->pos / piece);
-            if (h->piece_exec.size() != (size_t)(nit / piece)) {
-                h->piece_exec.assign((size_t)(nit / piece), nullptr);
-                h->piece_launches.assign((size_t)(nit / piece), 0);
-                h->piece_stage_launches.assign((size_t)(nit / piece), 0);
-            }
-            if (!h->piece_exec[k] && !capture_iters(h, h->pos, piece, nit, &h->piece_exec[k], &h->piece_launches[k],
-                                                    &h->piece_stage_launches[k])) {
-                h->graph_off = true;
-                continue;
-            }
-            MR_CK(cudaGraphLaunch(h->piece_exec[k], h->stream));
-            h->K.n += h->piece_launches[k];
-            h->stage_launches += h->piece_stage_launches[k];
-            advance(piece);
             continue;
         }
         MR_TRY(iteration(h, h->pos, nit, part_of(h, h->pos)));
@@ -909,8 +889,8 @@ mr_status run_iters(mr_solver* h, double dt, long long n)
 mr_status cfl_enqueue(mr_solver* h, unsigned long long* bits)
 {
     Grid& g = h->K.g;
-    // free node slots, for the capacity rule at this macro-step boundary
-    MR_CK(cudaMemcpyAsync(h->h_top, g.ftop, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    // free node slots and the halt record, for the capacity rule at this boundary
+    MR_TRY(enqueue_slot_record(h));
     if (h->wmax_valid) { // computed at the end of the macro-step kernel that led to this state
         MR_CK(cudaMemcpyAsync(bits, g.wmax, sizeof *bits, cudaMemcpyDeviceToHost, h->stream));
         return MR_OK;
@@ -1315,6 +1295,11 @@ mr_status mr_step(mr_solver* h, double t_target, long long* iters_out)
         double dt;
         MR_TRY(head_enqueue(h)); // read back with the CFL speed
         MR_TRY(cfl_dt(h, &dt));
+        if (h->h_top[2]) { // the macro step before halted: finish it, then this boundary again
+            MR_TRY(recover(h));
+            MR_TRY(run_iters(h, h->dt, 0));
+            continue;
+        }
         MR_TRY(head_finish(h));
         bool last = false;
         if (h->t + nit * dt >= t_target * (1.0 - 1e-14)) {
@@ -1373,7 +1358,7 @@ mr_status mr_set_grid_cap(mr_solver* h, int ctas)
     if (h->K.g.gcap == ctas) return MR_OK;
     // a captured macro step holds the old launch shape: drop it once the
     // stream has passed it, and capture again at the next macro step
-    if (h->macro_exec || h->head_exec || !h->piece_exec.empty()) {
+    if (h->macro_exec || h->head_exec) {
         MR_CK(cudaStreamSynchronize(h->stream));
         drop_graphs(h);
     }
@@ -1614,7 +1599,8 @@ mr_status mr_release_cached_memory(void)
 // call waits, so every problem runs at the pace of its own stream.
 namespace {
 
-enum { PG_IDLE = 0, PG_WAIT = 1, PG_DONE = 2 };
+// PG_SETTLE: the last macro step is queued, its halt record on the way
+enum { PG_IDLE = 0, PG_WAIT = 1, PG_DONE = 2, PG_SETTLE = 3 };
 
 struct Progress {
     int phase = PG_IDLE;
@@ -1631,6 +1617,16 @@ mr_status progress_start(mr_solver* h, unsigned long long* bits, cudaEvent_t ev,
     return MR_OK;
 }
 
+// the end of a problem's last macro step: its halt record read back before
+// it counts as done
+mr_status settle_start(mr_solver* h, cudaEvent_t ev, Progress* pg)
+{
+    MR_TRY(enqueue_slot_record(h));
+    MR_CK(cudaEventRecord(ev, h->stream));
+    pg->phase = PG_SETTLE;
+    return MR_OK;
+}
+
 // one non-blocking attempt; returns true when the problem made progress
 bool progress_poll(mr_solver* h, double t_target, unsigned long long* bits, const int* err, cudaEvent_t ev,
                    Progress* pg)
@@ -1643,11 +1639,20 @@ bool progress_poll(mr_solver* h, double t_target, unsigned long long* bits, cons
     }
     const cudaError_t e = cudaEventQuery(ev);
     if (e == cudaErrorNotReady) return false;
+    const bool settling = pg->phase == PG_SETTLE;
     pg->phase = PG_DONE;
     if (e != cudaSuccess) {
         pg->status = MR_E_CUDA;
         return true;
     }
+    if (h->h_top[2]) { // a remesh of the previous macro step halted: finish it, then this boundary again
+        pg->status = recover(h);
+        if (pg->status == MR_OK) pg->status = run_iters(h, h->dt, 0);
+        if (pg->status == MR_OK) pg->status = settling ? settle_start(h, ev, pg) : progress_start(h, bits, ev, pg);
+        if (pg->status != MR_OK) pg->phase = PG_DONE;
+        return true;
+    }
+    if (settling) return true; // done: its last macro step completed without a halt
     if (*err) { // the finiteness check of the previous macro step failed
         pg->status = sync_check(h);
         if (pg->status == MR_OK) pg->status = MR_E_NUMERIC;
@@ -1665,8 +1670,8 @@ bool progress_poll(mr_solver* h, double t_target, unsigned long long* bits, cons
     const double t0 = h->t;
     pg->status = run_iters(h, dt, nit);
     h->t = last ? t_target : t0 + nit * dt;
-    if (pg->status == MR_OK && !last) {
-        pg->status = progress_start(h, bits, ev, pg);
+    if (pg->status == MR_OK) {
+        pg->status = last ? settle_start(h, ev, pg) : progress_start(h, bits, ev, pg);
         if (pg->status != MR_OK) pg->phase = PG_DONE;
     }
     return true;
@@ -1836,7 +1841,8 @@ struct mr_request {
     mr_config cfg{};
     std::vector<double> q0;
     double t_end = 0.0;
-    size_t bytes = 0;       // projected device footprint
+    size_t proj = 0;        // projected device footprint
+    size_t bytes = 0;       // charged: the larger of proj and the solver's footprint
     int slot = -1;          // pinned host slot while admitted
     mr_solver* h = nullptr;
     cudaStream_t st = nullptr;
@@ -1936,7 +1942,7 @@ mr_status admit(mr_server* s)
         q->h->async_err = &s->errs[q->slot];
         q->h->launch_mode = MR_LAUNCH_GRAPH; // concurrent requests: as batch instances
         if (s->gcap) mr_set_grid_cap(q->h, s->gcap); // nothing captured yet: cannot fail
-        if (q->h->bytes > q->bytes) q->bytes = q->h->bytes; // the created tree needs more than projected
+        q->bytes = q->h->bytes > q->proj ? q->h->bytes : q->proj; // a new tree holds room for every cell
         s->used += q->bytes;
         q->state = q->h->t < q->t_end ? 1 : 2;
         if (q->state == 1) s->active.push_back(q);
@@ -2013,7 +2019,7 @@ mr_status mr_server_submit(mr_server* s, const mr_config* cfg, const double* q0,
     if (!q) return MR_E_NOMEM;
     q->cfg = *cfg;
     q->t_end = t_end;
-    q->bytes = projected_bytes(cfg);
+    q->bytes = q->proj = projected_bytes(cfg);
     if (q->bytes > s->budget) {
         delete q;
         s->err = "submit: the request alone exceeds the memory budget";
@@ -2039,10 +2045,10 @@ mr_status mr_server_advance(mr_server* s, int* n_active, int* n_queued)
     std::vector<mr_request*> still;
     for (mr_request* q : s->active) {
         progress_poll(q->h, q->t_end, &s->bits[q->slot], &s->errs[q->slot], q->ev, &q->pg);
-        if (q->h->bytes > q->bytes) { // its node arrays grew: charged from now on
-            s->used += q->h->bytes - q->bytes;
-            q->bytes = q->h->bytes;
-        }
+        const size_t charge = q->h->bytes > q->proj ? q->h->bytes : q->proj; // after a resize of its node arrays
+        s->used += charge;
+        s->used -= q->bytes;
+        q->bytes = charge;
         if (q->pg.phase == PG_DONE) {
             q->status = q->pg.status;
             cudaEventRecord(q->fin, q->st);

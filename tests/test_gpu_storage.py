@@ -78,3 +78,28 @@ def test_blast_3d_L8_mixed_fits_in_2GB():
     print(f"3D L=8 mixed: {st['leaves']} leaves, {st['node_slots']} slots, "
           f"{st['device_bytes'] / 2**30:.2f} GiB")
     s.close()
+
+
+def test_batch_instances_recover_from_halts_bitwise():
+    """batch instances read the halt record at their next boundary instead of
+    every 16 fine iterations: a fast-growing tree (2D Euler quadrants, L = 9,
+    the opening phase) halts and resumes, with results bitwise those of the
+    standalone solver"""
+    import paper_1905_08717_gb300 as pkg
+    probs = [I.euler_2d_quadrants(L=9, eps=1e-3, seed=s) for s in (2, 3)]
+    b = pkg.Batch([p for p, _ in probs], [q for _, q in probs])
+    b.step(0.06)
+    halts = 0
+    for (p, q), inst in zip(probs, b.instances):
+        s = pkg.Solver(p, q)
+        s.set_launch_mode(pkg.MR_LAUNCH_GRAPH)
+        s.step(0.06)
+        ka, va = inst.leaves()
+        kb, vb = s.leaves()
+        assert np.array_equal(ka, kb) and np.array_equal(va, vb)
+        st = inst.stats()
+        assert st["node_slots"] >= st["nodes"] and st["pos"] == 0
+        halts += st["halts"]
+        s.close()
+    print(f"batch of 2: {halts} halts")
+    b.close()
