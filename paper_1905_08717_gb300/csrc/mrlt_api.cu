@@ -213,7 +213,7 @@ mr_status dev_alloc(mr_solver* h, T** p, size_t count)
 // need + 2 margin.  Inside a macro step (adaptation at every fine iteration,
 // on the levels that are active) every remesh first checks on the device
 // that its tree fits, and halts the solver's device work if it does not
-// (k_room).  The host reads the halt record at the end of the macro step (a
+// (room_decide).  The host reads the halt record at the end of the macro step (a
 // solver that waits) or with the CFL speed at the next boundary (batch and
 // server instances); after a halt it grows the arrays to the flagged tree
 // plus two margins of a quarter of it and resumes at the halted remesh.
@@ -356,6 +356,7 @@ mr_status count_nodes(mr_solver* h, long long* used)
 // cell until the next macro-step boundary)
 mr_status fit_new_tree(mr_solver* h)
 {
+    MR_CK(cudaMemsetAsync(h->K.g.flag, 0, (size_t)h->ntot, h->stream)); // (see adapt)
     long long used = 0;
     MR_TRY(count_nodes(h, &used));
     h->used_macro = used;
@@ -541,9 +542,8 @@ mr_status adapt(mr_solver* h, int la, int part = 0, long long it = 0)
             h->K.scale_init();
             for (int l = g.lb; l <= g.L; ++l) h->K.scale(l);
         }
-        h->K.clear_flags(g.off[la], h->ntot);
-        h->K.mark_refinements(la);
-        if (part == 0 && can_halt(h)) h->K.check_room(la, it);
+        // the flags are zero here: every remesh's compaction clears those it set
+        h->K.mark_refinements(la, part == 0 && can_halt(h) ? it : -1);
     }
     if (part != 1) {
         h->K.apply_tree(la);

@@ -45,25 +45,28 @@ __global__ void k_detail(const __grid_constant__ Grid g, int lo, int hi)
     dev_detail<D, M, T>(g, lo, hi);
 }
 
+// Desired and admissible refinements in one pass: a cell's admissibility
+// reads only its own desire bit (set by the same thread, same grid-stride
+// order), and desire reads only the detail bits, which admissibility keeps.
+// it >= 0: this launch finalises the refinement flags (a remesh at level
+// la = L-1 has no closure), so it also checks that the new tree fits.
 template <int D>
-__global__ void k_desire(const __grid_constant__ Grid g, int lo, int hi, int la)
+__global__ void k_mark(const __grid_constant__ Grid g, int lo, int hi, int la, long long it)
 {
     MRLT_ENTER(g);
     dev_desire<D>(g, lo, hi, la);
-}
-
-template <int D>
-__global__ void k_allow(const __grid_constant__ Grid g, int lo, int hi, int la)
-{
-    MRLT_ENTER(g);
     dev_allow<D>(g, lo, hi, la);
+    if (it >= 0) room_decide(g, refined_here(g, la), la, it);
 }
 
+// it >= 0: the last closure (level l-1 = la), which also checks that the new
+// tree fits; its threads read back the level-la flags they wrote themselves
 template <int D>
-__global__ void k_close(const __grid_constant__ Grid g, int l)
+__global__ void k_close(const __grid_constant__ Grid g, int l, long long it)
 {
     MRLT_ENTER(g);
     dev_close<D>(g, l);
+    if (it >= 0) room_decide(g, refined_here(g, l - 1), l - 1, it);
 }
 
 template <int D, int M, class T>
@@ -73,11 +76,24 @@ __global__ void k_apply(const __grid_constant__ Grid g, int l, int la)
     dev_apply<D, M, T>(g, l, la);
 }
 
-// compaction of levels lo..hi: chunks of NTHREADS cells, one block each
-__global__ void k_cmp_count(const __grid_constant__ Grid g, LevelChunks lc, int* bc)
+// the releases of a remesh and its installation on level la in one launch:
+// level la creates no node (its nodes stay; only leaf and internal swap), so
+// it takes no slot, and the released nodes (levels above la) are not its
+template <int D, int M, class T>
+__global__ void k_release_apply(const __grid_constant__ Grid g, int la)
+{
+    MRLT_ENTER(g);
+    dev_release(g, la);
+    dev_apply<D, M, T>(g, la, la);
+}
+
+// compaction of levels lo..hi: chunks of NTHREADS cells, one block each;
+// the tile flags of those levels [t0, t1) cleared for the scatter
+__global__ void k_cmp_count(const __grid_constant__ Grid g, LevelChunks lc, int* bc, long long t0, long long t1)
 {
     MRLT_ENTER(g);
     chunk_count<NTHREADS>(g, lc, blockIdx.x, bc);
+    MRLT_GRID_STRIDE(i, t1 - t0) g.tflag[t0 + i] = 0;
 }
 
 // exclusive scan of the per-chunk counts, one block per level
@@ -271,31 +287,28 @@ void Launcher::leaf_copy(int lo, int hi, int from, int to)
 }
 
 template <int D, int M>
-static void adapt_dm(Launcher& L, int la)
+static void adapt_dm(Launcher& L, int la, long long it)
 {
     const Grid& g = L.g;
     const int hi = g.L - 1; // levels whose nodes may own children
     if (g.prec) pdl_launch(k_detail<D, M, float>, blocks_list(g, hi), NTHREADS, 0, L.st, g, la, hi);
     else pdl_launch(k_detail<D, M, double>, blocks_list(g, hi), NTHREADS, 0, L.st, g, la, hi);
-    pdl_launch(k_desire<D>, blocks_dense(g.N[hi]), NTHREADS, 0, L.st, g, la, hi, la);
-    pdl_launch(k_allow<D>, blocks_dense(g.N[hi]), NTHREADS, 0, L.st, g, la, hi, la);
-    L.n += 3;
-    for (int l = g.L - 1; l > la; --l, ++L.n) pdl_launch(k_close<D>, blocks_dense(g.N[l - 1]), NTHREADS, 0, L.st, g, l);
+    pdl_launch(k_mark<D>, blocks_dense(g.N[hi]), NTHREADS, 0, L.st, g, la, hi, la, la == hi ? it : -1LL);
+    L.n += 2;
+    for (int l = g.L - 1; l > la; --l, ++L.n)
+        pdl_launch(k_close<D>, blocks_dense(g.N[l - 1]), NTHREADS, 0, L.st, g, l, l == la + 1 ? it : -1LL);
 }
 
-__global__ void k_release(const __grid_constant__ Grid g, int la)
-{
-    MRLT_ENTER(g);
-    dev_release(g, la);
-}
 
 template <int D, int M>
 static void apply_dm(Launcher& L, int la)
 {
     const Grid& g = L.g;
-    pdl_launch(k_release, blocks_list(g, g.L), NTHREADS, 0, L.st, g, la);
+    const int b0 = blocks_list(g, g.L), b1 = blocks_dense(g.N[la]);
+    if (g.prec) pdl_launch(k_release_apply<D, M, float>, b0 > b1 ? b0 : b1, NTHREADS, 0, L.st, g, la);
+    else pdl_launch(k_release_apply<D, M, double>, b0 > b1 ? b0 : b1, NTHREADS, 0, L.st, g, la);
     ++L.n;
-    for (int l = la; l <= g.L; ++l, ++L.n) {
+    for (int l = la + 1; l <= g.L; ++l, ++L.n) {
         if (g.prec) pdl_launch(k_apply<D, M, float>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
         else pdl_launch(k_apply<D, M, double>, blocks_dense(g.N[l]), NTHREADS, 0, L.st, g, l, la);
     }
@@ -311,7 +324,7 @@ static void apply_dm(Launcher& L, int la)
         else fn<3, 5>(__VA_ARGS__);                                 \
     } while (0)
 
-void Launcher::mark_refinements(int la) { MRLT_DM_DISPATCH(adapt_dm, *this, la); }
+void Launcher::mark_refinements(int la, long long it) { MRLT_DM_DISPATCH(adapt_dm, *this, la, it); }
 void Launcher::apply_tree(int la) { MRLT_DM_DISPATCH(apply_dm, *this, la); }
 
 void Launcher::compact(int lo, int hi)
@@ -325,9 +338,8 @@ void Launcher::compact(int lo, int hi)
         total += (int)((g.N[l] + NTHREADS - 1) / NTHREADS);
     }
     lbk.base[hi + 1] = total;
-    cudaMemsetAsync(g.tflag + g.toff[lo], 0,
-                    (size_t)(g.toff[hi] - g.toff[lo]) + (size_t)g.ntx[hi] * g.nty[hi] * g.ntz[hi], st);
-    pdl_launch(k_cmp_count, total, NTHREADS, 0, st, g, lbk, bc);
+    const long long t0 = g.toff[lo], t1 = g.toff[hi] + (long long)g.ntx[hi] * g.nty[hi] * g.ntz[hi];
+    pdl_launch(k_cmp_count, total, NTHREADS, 0, st, g, lbk, bc, t0, t1);
     pdl_launch(k_cmp_scan, hi - lo + 1, 1024, 0, st, g, lbk, bc);
     pdl_launch(k_cmp_scatter, total, NTHREADS, 0, st, g, lbk, (const int*)bc);
     pdl_launch(k_tile_list, hi - lo + 1, 1024, 0, st, g, lo);
@@ -457,62 +469,6 @@ void Launcher::count_refined(int la, int* out)
     ++n;
 }
 
-// Does the tree flagged by the remesh at level la of fine iteration it fit
-// the node arrays?  The blocks count the refinement flags of levels
-// la..L-1 into room[0]; the new tree has 2^d nodes above level la per flag,
-// and the slots it may take are the free ones plus those of the nodes above
-// level la now (the remesh releases them first).  The last block to finish
-// (ticket room[3]) decides: short of slots, the solver halts at this
-// iteration, room[1] = it + 1, room[2] = the nodes of the new tree.
-__global__ void k_room(const __grid_constant__ Grid g, int la, long long it)
-{
-    MRLT_ENTER(g);
-    __shared__ int blk;
-    if (threadIdx.x == 0) blk = 0;
-    __syncthreads();
-    const long long from = g.off[la], to = g.off[g.L];
-    int c = 0;
-    GRID_STRIDE(i, to - from) c += (g.flag[from + i] & FL_REF) ? 1 : 0;
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&blk, c);
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    if (blk) atomicAdd(&g.room[0], blk);
-    __threadfence();
-    if (atomicAdd(&g.room[3], 1) != (int)gridDim.x - 1) return;
-    __threadfence();
-    const long long fresh = (long long)atomicExch(&g.room[0], 0) << g.d;
-    g.room[3] = 0;
-    long long above = 0, below = 0;
-    for (int l = g.lb; l <= g.L; ++l) {
-        const long long n = (long long)g.counts[l] + g.counts[LMAX + 1 + l];
-        if (l > la) above += n;
-        else below += n;
-    }
-    if (fresh > g.ftop[0] + above) {
-        g.room[2] = (int)(below + fresh);
-        g.room[1] = (int)(it + 1);
-    }
-}
-
-void Launcher::check_room(int la, long long it)
-{
-    pdl_launch(k_room, blocks_dense(g.off[g.L] - g.off[la]), NTHREADS, 0, st, g, la, it);
-    ++n;
-}
-
-// adaptation flags of cells [from, to) cleared
-__global__ void k_clear_flags(const __grid_constant__ Grid g, long long from, long long to)
-{
-    MRLT_ENTER(g);
-    dev_clear_flags(g, from, to);
-}
-
-void Launcher::clear_flags(long long from, long long to)
-{
-    pdl_launch(k_clear_flags, blocks_dense(to - from), NTHREADS, 0, st, g, from, to);
-    ++n;
-}
 
 // Compacting copy into node arrays of a new capacity: the nodes of level l
 // (leaves, then internal nodes, in list order) take the consecutive slots

@@ -14,7 +14,7 @@ struct Launcher {
 
     void project(int l, int mode);
     void leaf_copy(int lo, int hi, int from, int to); // leaves of levels lo..hi
-    void mark_refinements(int la);
+    void mark_refinements(int la, long long it = -1); // it >= 0: check that the tree fits (halt)
     void apply_tree(int la);
     void compact(int lo, int hi);                      // leaf / node / tile lists of levels lo..hi
     void reflux(int lo, int hi);                       // coarse levels lo..hi
@@ -27,8 +27,6 @@ struct Launcher {
     // compacting copy of the nodes from `from` into the arrays of g (a new capacity)
     void renumber(const Grid& from, const int* counts_host, long long used);
     void count_refined(int la, int* out);   // *out = refinement flags of levels la..L-1
-    void check_room(int la, long long it);  // halt unless the flagged tree fits (k_room)
-    void clear_flags(long long from, long long to);
     void finite(int l);
     void mass(int l, double* part);
     void pack(int l, long long base, int* keys, double* vals);

@@ -328,6 +328,53 @@ __device__ __forceinline__ void dev_close(const Grid& g, int l)
     }
 }
 
+// Does the tree flagged by a remesh at level la (fine iteration it) fit the
+// node arrays?  Each thread of the kernel that finalises the flags counted
+// `c` refined cells (the kernel's cells of levels la..L-1 in one flat
+// grid-stride range over them); the blocks add their counts into room[0].
+// The new tree has 2^d nodes above level la per refined cell, and the slots
+// it may take are the free ones plus those of the nodes above level la now
+// (the remesh releases them first).  The last block to finish (ticket
+// room[3]) decides: short of slots, the solver halts at this iteration,
+// room[1] = it + 1, room[2] = the nodes of the new tree (see halted()).
+// Called by every thread of the block.
+__device__ __forceinline__ void room_decide(const Grid& g, int c, int la, long long it)
+{
+    __shared__ int blk;
+    if (threadIdx.x == 0) blk = 0;
+    __syncthreads();
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&blk, c);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (blk) atomicAdd(&g.room[0], blk);
+    __threadfence();
+    if (atomicAdd(&g.room[3], 1) != (int)gridDim.x - 1) return;
+    __threadfence();
+    const long long fresh = (long long)atomicExch(&g.room[0], 0) << g.d;
+    g.room[3] = 0;
+    long long above = 0, below = 0;
+    for (int l = g.lb; l <= g.L; ++l) {
+        const long long n = (long long)g.counts[l] + g.counts[LMAX + 1 + l];
+        if (l > la) above += n;
+        else below += n;
+    }
+    if (fresh > g.ftop[0] + above) {
+        g.room[2] = (int)(below + fresh);
+        g.room[1] = (int)(it + 1);
+    }
+}
+
+// refined cells among this thread's cells of the flat range [off[la], off[L])
+// (levels la..L-1), in the grid-stride order of the kernel's own pass
+__device__ __forceinline__ int refined_here(const Grid& g, int la)
+{
+    int c = 0;
+    const long long from = g.off[la];
+    MRLT_GRID_STRIDE(i, g.off[g.L] - from) c += (g.flag[from + i] & FL_REF) ? 1 : 0;
+    return c;
+}
+
 // Slots of the nodes a remesh removes (levels la+1..L: a node whose parent
 // is not refined any more), pushed on the free stack before the apply passes
 // pop slots for new nodes.  Walks the node lists of the tree being replaced.
@@ -444,6 +491,7 @@ __device__ __forceinline__ void chunk_count(const Grid& g, const LevelChunks& lc
     const long long N = g.N[l];
     const long long i = (long long)(chunk - lc.base[l]) * CH + threadIdx.x;
     const int s = i < N ? status(g, l, i) : 0;
+    if (i < N) g.flag[g.off[l] + i] = 0; // the remesh is installed: its flags are spent
     const unsigned bl = __ballot_sync(0xffffffffu, s == 1);
     const unsigned bi = __ballot_sync(0xffffffffu, s == 2);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
