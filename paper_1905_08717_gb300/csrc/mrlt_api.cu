@@ -207,7 +207,7 @@ mr_status dev_alloc(mr_solver* h, T** p, size_t count)
 // head of the macro step).  The flags are counted (every refined cell owns
 // 2^d children), the count is read back together with the CFL speed, and
 // the arrays are resized before the tree is installed.  With need = max(nodes
-// in use, nodes of the next tree) and margin = max(the largest growth seen
+// in use, nodes of the next tree) and margin = max(2 x the largest growth seen
 // within the last macro step, a quarter of need, kMinSlots), arrays with
 // fewer than need + margin or more than need + 4 margin slots are set to
 // need + 2 margin.  Inside a macro step (adaptation at every fine iteration,
@@ -216,7 +216,8 @@ mr_status dev_alloc(mr_solver* h, T** p, size_t count)
 // (room_decide).  The host reads the halt record at the end of the macro step (a
 // solver that waits) or with the CFL speed at the next boundary (batch and
 // server instances); after a halt it grows the arrays to the flagged tree
-// plus two margins of a quarter of it and resumes at the halted remesh.
+// plus two margins of max(a quarter of it, 2 x its growth since the macro
+// step began) and resumes at the halted remesh.
 // Reservations made with mr_reserve_nodes are a floor.
 constexpr long long kMinSlots = 4096;
 constexpr size_t kDenseBytes = 32u << 20;
@@ -333,7 +334,7 @@ mr_status adjust_capacity(mr_solver* h, int top, long long next = -1)
     auto at_least = [](long long a, long long b) { return a > b ? a : b; };
     if (used - h->used_macro > h->grow_macro) h->grow_macro = used - h->used_macro;
     const long long need = at_least(used, next);
-    const long long margin = at_least(at_least(h->grow_macro, need / 4), kMinSlots);
+    const long long margin = at_least(at_least(2 * h->grow_macro, need / 4), kMinSlots);
     const long long target = clamp(need + 2 * margin + 1);
     h->used_macro = next >= 0 ? next : used;
     h->grow_macro = 0;
@@ -370,8 +371,8 @@ bool is_instance(const mr_solver* h) { return h->async_err && h->async_err != h-
 
 // Recovery from a halt whose record (h_top[2..3]) and free-slot count
 // (h_top[0]) were read back with the stream idle: the halt at iteration p
-// is cleared, the arrays grow to hold the flagged tree and two margins of a
-// quarter of it, and the position rewinds to p (into the macro step just
+// is cleared, the arrays grow to hold the flagged tree and two margins (see
+// the capacity rule), and the position rewinds to p (into the macro step just
 // counted complete, when pos is 0).  The caller then resumes with the
 // installation of p's tree (its flags are intact: nothing ran after them)
 // and launches the iterations after p again (h->redo, not counted twice).
@@ -394,6 +395,7 @@ mr_status recover(mr_solver* h)
     const long long used = g.cap - 1 - h->h_top[0];
     const long long need = tree > used ? tree : used;
     long long margin = need / 4;
+    if (margin < 2 * (need - h->used_macro)) margin = 2 * (need - h->used_macro); // a fast-growing tree
     if (margin < kMinSlots) margin = kMinSlots;
     long long target = need + 2 * margin + 1;
     if (target < h->reserved + 1) target = h->reserved + 1;
