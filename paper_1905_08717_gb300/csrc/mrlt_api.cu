@@ -550,7 +550,7 @@ mr_status adapt(mr_solver* h, int la, int part = 0, long long it = 0)
     if (part != 1) {
         h->K.apply_tree(la);
         h->K.compact(la, g.L);
-        for (int l = g.L - 1; l >= la; --l) h->K.project(l, PM_Q0);
+        h->K.project_up(g.L - 1, la, PM_Q0);
     }
     return MR_OK;
 }
@@ -564,20 +564,20 @@ mr_status lt_iteration(mr_solver* h, long long n, long long nit, int part = 0)
     const int L = g.L, lb = g.lb, lmin = level_min(h, n);
     if (part != 2) {
         h->K.leaf_copy(lmin, L, F_QE, F_Q0);
-        for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_Q0);
+        h->K.project_up(L - 1, lmin, PM_Q0);
     }
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
         MR_TRY(adapt(h, lmin, part, n));
     if (part == 1) return MR_OK;
     if (lmin > lb) h->K.project(lmin - 1, PM_MID);
     stage(h, lmin, L, 1, lmin); // first stage: all active levels at once
-    for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF2);
+    h->K.project_up(L - 1, lmin, PM_REF2);
     for (int l = L; l >= lmin; --l) {
         if (l < L) h->K.project(l, PM_PRJ2);
         stage(h, l, l, 2, lmin);
     }
     if (g.rk == 3) {
-        for (int l = L - 1; l >= lmin; --l) h->K.project(l, PM_REF3);
+        h->K.project_up(L - 1, lmin, PM_REF3);
         for (int l = L; l >= lmin; --l) {
             if (l < L) h->K.project(l, PM_PRJ3);
             stage(h, l, l, 3, lmin);
@@ -597,16 +597,16 @@ mr_status gts_iteration(mr_solver* h, long long n, int part = 0)
     const int L = g.L, lb = g.lb;
     if (part != 2) {
         h->K.leaf_copy(lb, L, F_QE, F_Q0);
-        for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q0);
+        h->K.project_up(L - 1, lb, PM_Q0);
     }
     if (h->cfg.adapt_mode == MR_ADAPT_EVERY || (h->cfg.adapt_mode == MR_ADAPT_MACRO && n == 0))
         MR_TRY(adapt(h, lb, part, n));
     if (part == 1) return MR_OK;
     stage(h, lb, L, 1, lb); // every level at the same instant: one launch per stage
-    for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q1);
+    h->K.project_up(L - 1, lb, PM_Q1);
     stage(h, lb, L, 2, lb);
     if (g.rk == 3) {
-        for (int l = L - 1; l >= lb; --l) h->K.project(l, PM_Q2);
+        h->K.project_up(L - 1, lb, PM_Q2);
         stage(h, lb, L, 3, lb);
     }
     return MR_OK;

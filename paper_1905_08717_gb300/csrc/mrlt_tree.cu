@@ -38,6 +38,14 @@ __global__ void k_project(const __grid_constant__ Grid g, int l, int mode)
     dev_project<D, T>(g, l, mode);
 }
 
+// up-sweep of levels hi..lo in one launch (dev_project_up)
+template <int D, class T>
+__global__ void k_project_up(const __grid_constant__ Grid g, int hi, int lo, int mode)
+{
+    MRLT_ENTER(g);
+    dev_project_up<D, T>(g, hi, lo, mode);
+}
+
 template <int D, int M, class T>
 __global__ void k_detail(const __grid_constant__ Grid g, int lo, int hi)
 {
@@ -272,6 +280,37 @@ void Launcher::project(int l, int mode)
     if (g.d == 1) g.prec ? project_d<1, float>(*this, l, mode) : project_d<1, double>(*this, l, mode);
     else if (g.d == 2) g.prec ? project_d<2, float>(*this, l, mode) : project_d<2, double>(*this, l, mode);
     else g.prec ? project_d<3, float>(*this, l, mode) : project_d<3, double>(*this, l, mode);
+}
+
+// Up-sweep hi -> lo in groups of at most 6 / d + 1 levels per launch: a group
+// [glo, ghi] has 2^{d (ghi - glo)} <= 64 descendants per top node, so two top
+// nodes fit the NTHREADS = 128 threads of a CTA.
+template <int D, class T>
+static void project_up_d(Launcher& L, int hi, int lo, int mode)
+{
+    constexpr int kDepth = 6 / D;
+    static_assert((1 << (D * kDepth)) * 2 <= NTHREADS, "two top nodes per CTA");
+    for (int ghi = hi; ghi >= lo;) {
+        const int glo = ghi - kDepth > lo ? ghi - kDepth : lo;
+        if (glo == ghi) {
+            project_d<D, T>(L, ghi, mode);
+        } else {
+            const int tops = NTHREADS >> (D * (ghi - glo));
+            long long b = (L.g.N[glo] + tops - 1) / tops;
+            if (b > 1216) b = 1216;
+            pdl_launch(k_project_up<D, T>, (int)b, NTHREADS, 0, L.st, L.g, ghi, glo, mode);
+        }
+        ++L.n;
+        ghi = glo - 1;
+    }
+}
+
+void Launcher::project_up(int hi, int lo, int mode)
+{
+    if (hi < lo) return;
+    if (g.d == 1) g.prec ? project_up_d<1, float>(*this, hi, lo, mode) : project_up_d<1, double>(*this, hi, lo, mode);
+    else if (g.d == 2) g.prec ? project_up_d<2, float>(*this, hi, lo, mode) : project_up_d<2, double>(*this, hi, lo, mode);
+    else g.prec ? project_up_d<3, float>(*this, hi, lo, mode) : project_up_d<3, double>(*this, hi, lo, mode);
 }
 
 template <class T>

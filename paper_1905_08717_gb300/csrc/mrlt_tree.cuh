@@ -13,6 +13,7 @@ struct Launcher {
     long long n = 0;   // kernel launches issued
 
     void project(int l, int mode);
+    void project_up(int hi, int lo, int mode); // levels hi..lo, fewer launches
     void leaf_copy(int lo, int hi, int from, int to); // leaves of levels lo..hi
     void mark_refinements(int la, long long it = -1); // it >= 0: check that the tree fits (halt)
     void apply_tree(int la);

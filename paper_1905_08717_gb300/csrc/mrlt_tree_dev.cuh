@@ -50,13 +50,92 @@ __device__ __forceinline__ void dev_leaf_copy(const Grid& g, int lo, int hi, int
 //  PM_PRJ3: Alg. 6 -- q** = mean(children at t^n + dt_{l+1}), end value
 //           2 q** - q^n (Eq. 16 with the theta values implied by q**)
 //  PM_MID:  Alg. 3 / Sec. 4.3 refresh of the mid-step level lmin-1
+// one internal node (l, id): the projection of the given mode
+template <int D, class T>
+__device__ __forceinline__ void project_node(const Grid& g, int l, long long id, int mode)
+{
+    constexpr int NCH = 1 << D;
+    int c[3];
+    cell_xyz(g, l, id, c);
+    int csl[NCH];
+    uint8_t cst[NCH];
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const long long ch = cell_id(g, l + 1, 2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
+                                     D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
+        cst[k] = status(g, l + 1, ch);
+        csl[k] = slot_of(g, l + 1, ch);
+    }
+    const int sl = slot_of(g, l, id);
+    T* q0 = nd<T>(g, F_Q0, sl);
+    T* q1 = nd<T>(g, F_Q1, sl);
+    T* q2 = nd<T>(g, F_Q2, sl);
+    T* qe = nd<T>(g, F_QE, sl);
+    for (int v = 0; v < g.m; ++v) {
+        const int o = v;
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) {
+            const T* c0 = nd<T>(g, F_Q0, csl[k]);
+            const T* c1 = nd<T>(g, F_Q1, csl[k]);
+            const T* c2 = nd<T>(g, F_Q2, csl[k]);
+            const T* ce = nd<T>(g, F_QE, csl[k]);
+            const int oc = v;
+            T w;
+            switch (mode) {
+            case PM_Q0: w = c0[oc]; break;
+            case PM_Q1: case PM_REF2: w = c1[oc]; break;
+            case PM_Q2: case PM_REF3: w = c2[oc]; break;
+            case PM_PRJ2:
+                if (cst[k] == 1) w = g.rk == 2 ? T(2) * ce[oc] - c0[oc] : T(4) * c2[oc] - T(3) * c0[oc];
+                else w = T(2) * c1[oc] - c0[oc];
+                break;
+            case PM_PRJ3: w = ce[oc]; break;
+            default: w = c0[oc]; break; // PM_MID: children at t^n
+            }
+            acc += w;
+        }
+        const T mean = acc * T(1.0 / NCH);
+        switch (mode) {
+        case PM_Q0: q0[o] = mean; break;
+        case PM_Q1: case PM_PRJ2: q1[o] = mean; break;
+        case PM_Q2: q2[o] = mean; break;
+        case PM_REF2:
+            nd<T>(g, F_XH, sl)[o] = mean;
+            q1[o] = T(2) * mean - q0[o];
+            break;
+        case PM_REF3: {
+            nd<T>(g, F_N1, sl)[o] = mean;
+            nd<T>(g, F_N3, sl)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * mean;
+            q2[o] = T(-5.5) * q0[o] - T(1.5) * q1[o] + T(8) * mean;
+            break;
+        }
+        case PM_PRJ3:
+            q2[o] = mean;
+            qe[o] = T(2) * mean - q0[o];
+            break;
+        default: { // PM_MID
+            if (g.rk == 2) {
+                nd<T>(g, F_NH, sl)[o] = mean;
+                qe[o] = T(-2) * q0[o] - q1[o] + T(4) * mean;
+            } else {
+                q2[o] = mean;
+                qe[o] = T(2) * mean - q0[o];
+                const T n1 = (mean + T(5.5) * q0[o] + T(1.5) * q1[o]) * T(0.125);
+                nd<T>(g, F_N1, sl)[o] = n1;
+                nd<T>(g, F_N3, sl)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * n1;
+            }
+        }
+        }
+    }
+}
+
 template <int D, class T>
 __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
 {
     const int cnt = g.counts[LMAX + 1 + l];
     const int* list = g.inner + g.off[l];
     const long long N = g.N[l];
-    constexpr int NCH = 1 << D;
     MRLT_GRID_STRIDE(t, cnt)
     {
         const long long id = list[t];
@@ -64,78 +143,48 @@ __device__ __forceinline__ void dev_project(const Grid& g, int l, int mode)
             atomicOr(g.err, ERR_INDEX);
             continue;
         }
-        int c[3];
-        cell_xyz(g, l, id, c);
-        int csl[NCH];
-        uint8_t cst[NCH];
-#pragma unroll
-        for (int k = 0; k < NCH; ++k) {
-            const long long ch = cell_id(g, l + 1, 2 * c[0] + (k & 1), D > 1 ? 2 * c[1] + ((k >> 1) & 1) : 0,
-                                         D > 2 ? 2 * c[2] + ((k >> 2) & 1) : 0);
-            cst[k] = status(g, l + 1, ch);
-            csl[k] = slot_of(g, l + 1, ch);
-        }
-        const int sl = slot_of(g, l, id);
-        T* q0 = nd<T>(g, F_Q0, sl);
-        T* q1 = nd<T>(g, F_Q1, sl);
-        T* q2 = nd<T>(g, F_Q2, sl);
-        T* qe = nd<T>(g, F_QE, sl);
-        for (int v = 0; v < g.m; ++v) {
-            const int o = v;
-            T acc = T(0);
-#pragma unroll
-            for (int k = 0; k < NCH; ++k) {
-                const T* c0 = nd<T>(g, F_Q0, csl[k]);
-                const T* c1 = nd<T>(g, F_Q1, csl[k]);
-                const T* c2 = nd<T>(g, F_Q2, csl[k]);
-                const T* ce = nd<T>(g, F_QE, csl[k]);
-                const int oc = v;
-                T w;
-                switch (mode) {
-                case PM_Q0: w = c0[oc]; break;
-                case PM_Q1: case PM_REF2: w = c1[oc]; break;
-                case PM_Q2: case PM_REF3: w = c2[oc]; break;
-                case PM_PRJ2:
-                    if (cst[k] == 1) w = g.rk == 2 ? T(2) * ce[oc] - c0[oc] : T(4) * c2[oc] - T(3) * c0[oc];
-                    else w = T(2) * c1[oc] - c0[oc];
-                    break;
-                case PM_PRJ3: w = ce[oc]; break;
-                default: w = c0[oc]; break; // PM_MID: children at t^n
-                }
-                acc += w;
-            }
-            const T mean = acc * T(1.0 / NCH);
-            switch (mode) {
-            case PM_Q0: q0[o] = mean; break;
-            case PM_Q1: case PM_PRJ2: q1[o] = mean; break;
-            case PM_Q2: q2[o] = mean; break;
-            case PM_REF2:
-                nd<T>(g, F_XH, sl)[o] = mean;
-                q1[o] = T(2) * mean - q0[o];
-                break;
-            case PM_REF3: {
-                nd<T>(g, F_N1, sl)[o] = mean;
-                nd<T>(g, F_N3, sl)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * mean;
-                q2[o] = T(-5.5) * q0[o] - T(1.5) * q1[o] + T(8) * mean;
-                break;
-            }
-            case PM_PRJ3:
-                q2[o] = mean;
-                qe[o] = T(2) * mean - q0[o];
-                break;
-            default: { // PM_MID
-                if (g.rk == 2) {
-                    nd<T>(g, F_NH, sl)[o] = mean;
-                    qe[o] = T(-2) * q0[o] - q1[o] + T(4) * mean;
+        project_node<D, T>(g, l, id, mode);
+    }
+}
+
+// An up-sweep of one mode over levels hi..lo (hi - lo = depth >= 1) in one
+// launch.  Each step of a CTA takes `tops` internal nodes of level lo and
+// projects their internal descendants bottom-up, level by level, with a CTA
+// barrier between levels: a node's projection reads only its own children,
+// which lie in the same subtree.  Thread t of a step owns descendant t % sub
+// of top node t / sub on each level (sub = 2^{d (m - lo)} on level m), so
+// 2^{d depth} <= blockDim.x is required.  Every node is projected by the same
+// operations as in dev_project.
+template <int D, class T>
+__device__ __forceinline__ void dev_project_up(const Grid& g, int hi, int lo, int mode)
+{
+    const int depth = hi - lo;
+    const int tops = blockDim.x >> (D * depth);
+    const int cnt = g.counts[LMAX + 1 + lo];
+    const int* list = g.inner + g.off[lo];
+    const long long N = g.N[lo];
+    const int nstep = (cnt + tops - 1) / tops;
+    for (int c = blockIdx.x; c < nstep; c += gridDim.x) { // uniform across the CTA
+        for (int m = hi; m >= lo; --m) {
+            const int s = m - lo;
+            const int sub = 1 << (D * s);
+            const int t = threadIdx.x;
+            const int ti = c * tops + t / sub;
+            if (t < tops * sub && ti < cnt) {
+                const long long top = list[ti];
+                if (top < 0 || top >= N) {
+                    atomicOr(g.err, ERR_INDEX);
                 } else {
-                    q2[o] = mean;
-                    qe[o] = T(2) * mean - q0[o];
-                    const T n1 = (mean + T(5.5) * q0[o] + T(1.5) * q1[o]) * T(0.125);
-                    nd<T>(g, F_N1, sl)[o] = n1;
-                    nd<T>(g, F_N3, sl)[o] = T(-6.5) * q0[o] - T(1.5) * q1[o] + T(9) * n1;
+                    int tc[3];
+                    cell_xyz(g, lo, top, tc);
+                    const int r = t % sub, msk = (1 << s) - 1;
+                    const long long id = cell_id(g, m, (tc[0] << s) + (r & msk),
+                                                 D > 1 ? (tc[1] << s) + ((r >> s) & msk) : 0,
+                                                 D > 2 ? (tc[2] << s) + (r >> (2 * s)) : 0);
+                    if (status(g, m, id) == 2) project_node<D, T>(g, m, id, mode);
                 }
             }
-            }
+            __syncthreads();
         }
     }
 }
