@@ -59,6 +59,10 @@ def _args():
     ap.add_argument("--level", type=int, default=10, help="finest level (profiling runs)")
     ap.add_argument("--eps", type=float, default=1e-3, help="threshold (profiling runs)")
     ap.add_argument("--min-level", type=int, default=3, help="coarsest leaf level (profiling runs)")
+    ap.add_argument("--window", type=float, nargs=2, metavar=("T0", "K"), default=None,
+                    help="profiling run: solve to T0, then K fine iterations; prints how many stage launches "
+                         "come before those K iterations and the launches and leaf-stages within them "
+                         "(the launch window of a small ncu capture)")
     return ap.parse_args()
 
 
@@ -495,6 +499,29 @@ def _persistent(pkg, torch, p, qn, t_end: float) -> dict:
     return out
 
 
+def _profile_window(pkg, inputs, args, stream, rank):
+    """A window of K fine iterations of the profiling solve, after solving to
+    T0: the stage launches before the window (ncu -s), the stage launches and
+    leaf-stages within it (ncu -c, and the divisor of its DRAM bytes).  Every
+    stage launch is counted in profiling mode, which launches directly."""
+    p, q = inputs.euler_2d_quadrants(L=args.level, eps=args.eps, seed=0, min_level=args.min_level)
+    s = pkg.Solver(p, q, stream=stream)
+    s.profile(True)
+    t0, k = args.window[0], int(args.window[1])
+    s.step(t0)
+    a = s.profile_read()
+    s.iterate(s.stats()["dt"], k)
+    b = s.profile_read()
+    s.profile(False)
+    if rank == 0:
+        print(json.dumps({"profile_window": True, "level": args.level, "eps": args.eps, "t0": t0, "iterations": k,
+                          "stage_launches_before": a["stage_launches"],
+                          "stage_launches": b["stage_launches"] - a["stage_launches"],
+                          "leaf_stages": int(b["leaf_stages"].sum() - a["leaf_stages"].sum()),
+                          "leaves": s.stats()["leaves"]}))
+    s.close()
+
+
 def _cpu_baseline(seconds: float = 12.0) -> dict:
     """The FP64 oracle, as it stands, on the first fine iterations of the same
     solve (single host thread), until ~`seconds` of CPU work."""
@@ -560,6 +587,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
+    if args.profile_run and args.window is not None:
+        _profile_window(pkg, inputs, args, stream, rank)
+        return
     if args.profile_run:
         p, q = inputs.euler_2d_quadrants(L=args.level, eps=args.eps, seed=0, min_level=args.min_level)
     else:
