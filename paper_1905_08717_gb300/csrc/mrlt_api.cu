@@ -289,8 +289,14 @@ mr_status set_capacity(mr_solver* h, long long newcap, bool keep)
         drop_graphs(h);
     }
     const Grid from = g;
+    Grid ng = g; // the solver keeps its arrays if an allocation fails
     std::vector<void*> fresh;
-    MR_TRY(alloc_nodes(h, g, newcap, fresh));
+    const mr_status ra = alloc_nodes(h, ng, newcap, fresh);
+    if (ra != MR_OK) {
+        free_allocs(h, fresh);
+        return ra;
+    }
+    g = ng;
     if (keep) h->K.renumber(from, cnt, used);
     free_allocs(h, h->node_allocs);
     h->node_allocs.swap(fresh);
@@ -386,12 +392,6 @@ mr_status recover(mr_solver* h)
         h->err = "halt record out of range";
         return MR_E_STATE;
     }
-    MR_CK(cudaMemsetAsync(g.room, 0, 4 * sizeof(int), h->stream));
-    h->h_top[2] = h->h_top[3] = 0;
-    if (h->pos == 0) {
-        --h->macros;
-        h->head_pending = h->head_done = false; // the boundary's head ran halted: again
-    }
     const long long used = g.cap - 1 - h->h_top[0];
     const long long need = tree > used ? tree : used;
     long long margin = need / 4;
@@ -399,7 +399,14 @@ mr_status recover(mr_solver* h)
     if (margin < kMinSlots) margin = kMinSlots;
     long long target = need + 2 * margin + 1;
     if (target < h->reserved + 1) target = h->reserved + 1;
+    // grown first: if that fails the solver stays halted, and a later call retries
     MR_TRY(set_capacity(h, target, true));
+    MR_CK(cudaMemsetAsync(g.room, 0, 4 * sizeof(int), h->stream));
+    h->h_top[2] = h->h_top[3] = 0;
+    if (h->pos == 0) {
+        --h->macros;
+        h->head_pending = h->head_done = false; // the boundary's head ran halted: again
+    }
     if (need - h->used_macro > h->grow_macro) h->grow_macro = need - h->used_macro;
     h->redo += launched - p;
     h->pos = p;
@@ -1382,12 +1389,14 @@ mr_status mr_set_launch_mode(mr_solver* h, int mode)
 {
     if (!h || (mode != MR_LAUNCH_PERSISTENT && mode != MR_LAUNCH_GRAPH)) return MR_E_INVALID;
     if (h->pos != 0) return MR_E_STATE;
-    h->launch_mode = mode;
-    // the macro-step kernel installs trees without a host check: room for every cell
+    // the macro-step kernel installs trees without a host check: room for every
+    // cell first (the mode stays as it was if that fails)
     if (mode == MR_LAUNCH_PERSISTENT) {
         MR_TRY(set_capacity(h, h->ntot + 1, true));
         MR_TRY(sync_check(h));
     }
+    h->launch_mode = mode;
+    h->head_pending = h->head_done = false;
     return MR_OK;
 }
 

@@ -103,3 +103,57 @@ def test_batch_instances_recover_from_halts_bitwise():
         s.close()
     print(f"batch of 2: {halts} halts")
     b.close()
+
+
+def test_single_iterations_equal_whole_macro_steps_bitwise():
+    """one fine iteration per call (direct launches, a check point at the end
+    of every call) against whole macro steps in one call (graphs, check points
+    at macro-step ends): the same bits, with the default capacity rule and its
+    resizes, over twelve macro steps of a growing tree (2D Euler quadrants,
+    L = 9)"""
+    import paper_1905_08717_gb300 as pkg
+    p, q = I.euler_2d_quadrants(L=9, eps=1e-3, seed=3)
+    a, b = pkg.Solver(p, q), pkg.Solver(p, q)
+    dt = 3.0e-5
+    nit = 1 << (p.max_level - p.min_level)
+    n = 12 * nit + 5
+    for _ in range(n):
+        a.iterate(dt, 1)
+    b.iterate(dt, n)
+    ka, va = a.leaves()
+    kb, vb = b.leaves()
+    assert np.array_equal(ka, kb) and np.array_equal(va, vb)
+    sa, sb = a.stats(), b.stats()
+    assert sa["iters"] == sb["iters"] == n and sa["pos"] == sb["pos"] == 5
+    print(f"single iterations: {sa['halts']} halts; whole macro steps: {sb['halts']} halts")
+    a.close()
+    b.close()
+
+
+def test_persistent_mode_keeps_room_for_every_cell():
+    """switching to the persistent kernel (which installs trees without a host
+    check) gives the node arrays a slot for every cell; switching back
+    compacts them again at the next boundary, and the result matches a solve
+    that never switched to FP64 round-off"""
+    import paper_1905_08717_gb300 as pkg
+    p, q = I.euler_2d_quadrants(L=9, eps=1e-3, seed=2)
+    cells = sum(1 << (2 * l) for l in range(p.min_level, p.max_level + 1))
+    s, ref = pkg.Solver(p, q), pkg.Solver(p, q)
+    s.step(0.01)
+    ref.step(0.01)
+    assert s.stats()["node_slots"] < cells
+    s.set_launch_mode(pkg.MR_LAUNCH_PERSISTENT)
+    assert s.stats()["node_slots"] == cells
+    s.step(0.02)
+    ref.step(0.02)
+    s.set_launch_mode(pkg.MR_LAUNCH_GRAPH)
+    s.step(0.03)
+    ref.step(0.03)
+    assert s.stats()["node_slots"] < cells
+    ka, va = s.leaves()
+    kb, vb = ref.leaves()
+    assert np.array_equal(ka, kb)
+    scale = np.abs(vb).max(axis=0)
+    assert np.all(np.abs(va - vb) <= 1e-13 * (np.abs(vb) + scale))
+    s.close()
+    ref.close()
