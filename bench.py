@@ -59,6 +59,9 @@ def _args():
     ap.add_argument("--level", type=int, default=10, help="finest level (profiling runs)")
     ap.add_argument("--eps", type=float, default=1e-3, help="threshold (profiling runs)")
     ap.add_argument("--min-level", type=int, default=3, help="coarsest leaf level (profiling runs)")
+    ap.add_argument("--case", choices=["quadrants2d", "blast3d"], default="quadrants2d",
+                    help="profiling runs: the 2D Euler quadrants (default) or the 3D Euler blast")
+    ap.add_argument("--mixed", action="store_true", help="profiling runs: mixed precision")
     ap.add_argument("--window", type=float, nargs=2, metavar=("T0", "K"), default=None,
                     help="profiling run: solve to T0, then K fine iterations; prints how many stage launches "
                          "come before those K iterations and the launches and leaf-stages within them "
@@ -499,12 +502,21 @@ def _persistent(pkg, torch, p, qn, t_end: float) -> dict:
     return out
 
 
+def _profile_problem(inputs, args):
+    """the problem of a profiling run: --case at --level, --eps, --min-level"""
+    prec = inputs.PREC_MIXED if args.mixed else inputs.PREC_FP64
+    if args.case == "blast3d":
+        return inputs.euler_3d_blast(L=args.level, eps=args.eps, min_level=args.min_level, precision=prec)
+    p, q = inputs.euler_2d_quadrants(L=args.level, eps=args.eps, seed=0, min_level=args.min_level)
+    return p.replace(precision=prec), q
+
+
 def _profile_window(pkg, inputs, args, stream, rank):
     """A window of K fine iterations of the profiling solve, after solving to
     T0: the stage launches before the window (ncu -s), the stage launches and
     leaf-stages within it (ncu -c, and the divisor of its DRAM bytes).  Every
     stage launch is counted in profiling mode, which launches directly."""
-    p, q = inputs.euler_2d_quadrants(L=args.level, eps=args.eps, seed=0, min_level=args.min_level)
+    p, q = _profile_problem(inputs, args)
     s = pkg.Solver(p, q, stream=stream)
     s.profile(True)
     t0, k = args.window[0], int(args.window[1])
@@ -591,13 +603,13 @@ def run_ours(args):
         _profile_window(pkg, inputs, args, stream, rank)
         return
     if args.profile_run:
-        p, q = inputs.euler_2d_quadrants(L=args.level, eps=args.eps, seed=0, min_level=args.min_level)
+        p, q = _profile_problem(inputs, args)
     else:
         p, q = inputs.euler_2d_quadrants(L=10, eps=1e-3, seed=0)
     q_pin = torch.from_numpy(q).pin_memory()
     qn = q_pin.numpy()
     n = 1 << p.max_level
-    uni_pin = torch.empty(p.nvars() * n * n, dtype=torch.float64).pin_memory().numpy()
+    uni_pin = torch.empty(p.nvars() * n ** p.dim, dtype=torch.float64).pin_memory().numpy()
     solver = pkg.Solver(p, qn, stream=stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
@@ -643,6 +655,7 @@ def run_ours(args):
             print(json.dumps({"profile_run": True, "ms_per_step": 1e3 * total_s / args.steps,
                               "updates": updates, "stage_ms": prof["stage_ms"],
                               "stage_launches": prof["stage_launches"], "launches": launches,
+                              "case": args.case, "mixed": args.mixed,
                               "level": args.level, "eps": args.eps, "min_level": args.min_level,
                               "leaf_stages_per_level": [int(x) for x in ls],
                               "stage_ms_per_level": [round(float(x), 3) for x in prof["stage_ms_per_level"]]}))
