@@ -159,6 +159,28 @@ def test_mixed_full_size_first_iterations_leafwise():
     _check_leafwise(p, q, 0.5 / 1024 / 3.7, 4)
 
 
+@pytest.mark.slow
+def test_mixed_blast_3d_full_size():
+    """the 3D blast precision workload at its full size (L = 8, 256^3 finest),
+    Courant number about 0.3 summed over the three directions: four fine
+    iterations leaf by leaf against the FP64 oracle, then one whole macro step
+    (32 fine iterations, every lmin) by the L1 distance of the finest-grid
+    reconstructions, where threshold decisions may flip"""
+    p, q = I.euler_3d_blast(L=8, eps=1e-3, min_level=3)
+    dt = 1.0e-4
+    err, tol = _check_leafwise(p, q, dt, 4)
+    pm = p.replace(precision=I.PREC_MIXED)
+    gm, ref = _solver(pm, q), oracle.Oracle(p.replace(precision=I.PREC_FP64), q)
+    gm.iterate(dt, 32)
+    ref.iterate(dt, 32)
+    e = _rel_l1(gm.uniform(), ref.uniform())
+    tol32 = 32 * (6 * C_FLUX * U32 * 0.3 + C_STATE * U32) + U32 + p.eps * 1e-2
+    print(f"3D blast L=8 mixed: 4 iterations max leaf error {err:.2e} (bound {tol:.2e}); "
+          f"32 iterations relative L1 {e.max():.2e} (bound {tol32:.2e})")
+    assert e.max() <= tol32, (e, tol32)
+    assert e.max() > 1e-12
+
+
 def test_mixed_burgers_1d():
     p, q = I.burgers_1d(L=10, eps=1e-3)
     _check(p, q, 0.3)
