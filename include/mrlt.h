@@ -158,7 +158,10 @@ mr_status mr_iterate(mr_solver* h, double dt, long long n_iters, long long* iter
 
 /* Asynchronous mode (enable = 1): mr_iterate and mr_step return once their
  * work is enqueued on the solver's stream instead of after it has completed
- * (mr_step still waits for each macro step's CFL value, which sets its step).
+ * (mr_step still waits for each macro step's CFL value, which sets its step;
+ * a solver with compact node arrays and adaptation at every fine iteration
+ * also waits at the end of each macro step, and of each call, for the check
+ * that no remesh ran out of node slots -- see mr_create).
  * Errors found on the device, including the non-finite check after every
  * macro step, are reported by the next mr_sync (or by mr_set_async(h, 0),
  * which synchronises).  MR_E_STATE for an instance of a batch or server. */
